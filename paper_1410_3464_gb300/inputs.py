@@ -1,0 +1,191 @@
+"""Seeded synthetic inputs: node-type masks, initial densities, concentrations,
+solid volumes and parameter sets for the reactive two-phase LBM workloads.
+
+This module only builds inputs (numbers and masks).  It contains none of the
+method's arithmetic and imports neither the CUDA binding nor the CPU oracle, so
+both sides of a parity test can consume the same arrays.
+
+Node types: 0 liquid, 1 gas, 2 solid D(s), 3 solid F(s), 4 inert wall,
+5 inlet reservoir, 6 outlet reservoir.
+
+Workloads (sizes and structure of the paper's scene, Section 5: a mineral grain
+immersed in liquid with a gas phase, walls with 90 degree contact angle, tau = 1,
+D2Q5 transport with rest fraction J_0):
+
+  * bubble_grain(): 128x64 channel, one D(s) grain r=12 at (64,32), one gas
+    bubble r=10 at (24,32), species A (1.0) and B (0.0), A->B at k1=1e-3, B
+    consumed at the grain surface at k2=1e-3 (first-order dissolution).
+  * porous_discs(): seeded overlapping D(s) discs (radii U[8,24], porosity 0.6)
+    in an x-channel with an inlet reservoir column (alternating liquid and gas
+    slugs) and an outlet reservoir column; species B, E, F transported, A
+    derived from the liquid density; R1 (k1=1e-5, gas-producing), R3 (k3=1e-1),
+    R2 on D(s) (k2=1e-3), R4 on D(s)/F(s) (k4=1e-3).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+LIQUID, GAS, SOLID_D, SOLID_F, WALL, INLET, OUTLET = range(7)
+MAX_SPECIES = 4
+IDX_ABSENT = -1
+IDX_DERIVED = -2
+
+# Carnahan-Starling constants.  "Original" a=1, b=4, R=1 (critical temperature
+# 0.0943294 found numerically from dp/drho = d2p/drho2 = 0); "rescaled" set of
+# Section 3.1 (T_c = 0.999954).
+CS_ORIGINAL = dict(eos_a=1.0, eos_b=4.0, eos_R=1.0, Tc=0.0943294)
+CS_RESCALED = dict(eos_a=0.09926, eos_b=0.18727, eos_R=0.2, Tc=0.999954)
+# Coexistence densities (Maxwell equal-area construction) used only as initial
+# values: original EOS at 0.7 Tc, rescaled EOS at 0.7 Tc.
+COEX_ORIGINAL_07 = (0.35813, 0.009294)
+COEX_RESCALED_07 = (7.6495, 0.19852)
+
+
+def base_params(nx, ny):
+    """Parameter dictionary with every feature off and the paper's fluid
+    constants (G11=-1, G12=G21=0.001, a0=0.005, rho10=-0.008/ln a0, rho20=0.003,
+    tau=1)."""
+    return dict(
+        nx=int(nx), ny=int(ny), periodic_x=1, periodic_y=1,
+        tau=(1.0, 1.0), G11=-1.0, G12=0.001, G21=0.001,
+        a0=0.005, rho10=-0.008 / math.log(0.005), rho20=0.003,
+        w_adh=(0.0, 0.0), eos_a=1.0, eos_b=4.0, eos_R=1.0, eos_T=0.7 * CS_ORIGINAL["Tc"],
+        body_force=(0.0, 0.0), rho_ref=(1.0, 1.0),
+        n_species=0, idx_A=IDX_ABSENT, idx_B=IDX_ABSENT, idx_E=IDX_ABSENT, idx_F=IDX_ABSENT,
+        J0=(0.0,) * MAX_SPECIES, tau_g=(1.0,) * MAX_SPECIES, conc_ref=(0.0,) * MAX_SPECIES,
+        k1=0.0, inv_Keq=0.0, k3=0.0, k2=0.0, k4=0.0, C_F_sat=0.0,
+        gas_yield=0.0, inv_M_C=0.0, c_total_per_rho1=0.0,
+        Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=0,
+        rho_in_liq=(0.0, 0.0), rho_in_gas=(0.0, 0.0), rho_out=(0.0, 0.0),
+        inlet_period_liq=1, inlet_period_gas=0, conc_in=(0.0,) * MAX_SPECIES,
+    )
+
+
+def _pad(vals, fill=0.0):
+    vals = list(vals)
+    return tuple(vals + [fill] * (MAX_SPECIES - len(vals)))
+
+
+class Scene(dict):
+    """mask [ny,nx] u8, rho1, rho2 [ny,nx] f64, conc [ns,ny,nx] f64 (or None),
+    vol [2,ny,nx] f64 (or None), params dict."""
+
+
+def bubble_grain(nx=128, ny=64, grain=(64, 32, 12), bubble=(24, 32, 10),
+                 rho2_gas=0.002, rho2_liq=2e-5):
+    """Plain-method scene: x-periodic channel, wall rows y=0 and y=ny-1, one
+    D(s) grain, one gas bubble, liquid elsewhere at the coexistence densities of
+    the original C-S EOS at 0.7 T_c; species A=1.0, B=0.0."""
+    y, x = np.mgrid[0:ny, 0:nx]
+    mask = np.full((ny, nx), LIQUID, dtype=np.uint8)
+    gx, gy, gr = grain
+    bx, by, br = bubble
+    in_bubble = (x - bx) ** 2 + (y - by) ** 2 <= br * br
+    mask[in_bubble] = GAS
+    mask[(x - gx) ** 2 + (y - gy) ** 2 <= gr * gr] = SOLID_D
+    mask[0, :] = WALL
+    mask[ny - 1, :] = WALL
+    rl, rg = COEX_ORIGINAL_07
+    rho1 = np.where(mask == GAS, rg, rl).astype(np.float64)
+    rho2 = np.where(mask == GAS, rho2_gas, rho2_liq).astype(np.float64)
+    p = base_params(nx, ny)
+    p.update(periodic_x=1, periodic_y=0, rho_ref=(rl, rho2_liq),
+             n_species=2, idx_A=0, idx_B=1,
+             J0=_pad([1.0 / 3.0, 1.0 / 3.0]), tau_g=_pad([0.8, 0.8], 1.0),
+             conc_ref=_pad([1.0, 0.0]),
+             k1=1e-3, k2=1e-3, Vbar_D=1.0, seed=1)
+    conc = np.zeros((2, ny, nx))
+    conc[0] = 1.0
+    return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
+
+
+def _splitmix64_stream(seed):
+    """Seeded uniform stream in [0, 1) from the SplitMix64 generator."""
+    mask64 = (1 << 64) - 1
+    state = seed & mask64
+    while True:
+        state = (state + 0x9E3779B97F4A7C15) & mask64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask64
+        z ^= z >> 31
+        yield (z >> 11) * (1.0 / (1 << 53))
+
+
+def _liquid_spans_x(open_):
+    """True if a 4-connected path of open nodes joins column 0 to the last column."""
+    ny, nx = open_.shape
+    seen = np.zeros_like(open_)
+    stack = [(yy, 0) for yy in range(ny) if open_[yy, 0]]
+    for s in stack:
+        seen[s] = True
+    while stack:
+        yy, xx = stack.pop()
+        if xx == nx - 1:
+            return True
+        for dy, dx in ((0, 1), (1, 0), (0, -1), (-1, 0)):
+            a, b = yy + dy, xx + dx
+            if 0 <= a < ny and 0 <= b < nx and open_[a, b] and not seen[a, b]:
+                seen[a, b] = True
+                stack.append((a, b))
+    return False
+
+
+def discs_mask(nx, ny, seed, rmin=8.0, rmax=24.0, porosity=0.6, buffer=16, walls=True):
+    """Overlapping D(s) discs with centres uniform over the domain minus
+    `buffer` columns at each end, radii uniform in [rmin, rmax], added until the
+    solid fraction of the interior reaches 1 - porosity.  Reseeds (seed+1, ...)
+    until an open 4-connected path spans x.  Rows 0 and ny-1 are walls when
+    `walls` is set."""
+    y, x = np.mgrid[0:ny, 0:nx]
+    for attempt in range(64):
+        rng = _splitmix64_stream(seed + attempt)
+        solid = np.zeros((ny, nx), dtype=bool)
+        lo, hi = buffer, nx - buffer
+        target = 1.0 - porosity
+        interior = (x >= lo) & (x < hi)
+        area = interior.sum()
+        while solid[interior].sum() < target * area:
+            cx = lo + next(rng) * (hi - lo)
+            cy = next(rng) * ny
+            r = rmin + next(rng) * (rmax - rmin)
+            x0, x1 = max(int(cx - r) - 1, lo), min(int(cx + r) + 2, hi)
+            y0, y1 = max(int(cy - r) - 1, 0), min(int(cy + r) + 2, ny)
+            sub = (x[y0:y1, x0:x1] - cx) ** 2 + (y[y0:y1, x0:x1] - cy) ** 2 <= r * r
+            solid[y0:y1, x0:x1] |= sub
+        mask = np.where(solid, SOLID_D, LIQUID).astype(np.uint8)
+        if walls:
+            mask[0, :] = WALL
+            mask[ny - 1, :] = WALL
+        if _liquid_spans_x(mask == LIQUID):
+            return mask
+    raise RuntimeError("no spanning pore space found")
+
+
+def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
+                 k1=1e-5, k3=1e-1, k2=1e-3, k4=1e-3, rho2_gas=0.02, rho2_liq=4e-4,
+                 slug=(2000, 500)):
+    """Porous-medium scene with inflow of liquid and gas slugs; rescaled C-S
+    EOS at 0.7 T_c; species B, E, F transported and A derived."""
+    mask = discs_mask(nx, ny, seed, rmin, rmax, porosity)
+    mask[1:ny - 1, 0] = INLET
+    mask[1:ny - 1, nx - 1] = OUTLET
+    rl, rg = COEX_RESCALED_07
+    rho1 = np.where(mask == LIQUID, rl, 0.0)
+    rho2 = np.where(mask == LIQUID, rho2_liq, 0.0)
+    p = base_params(nx, ny)
+    p.update(periodic_x=0, periodic_y=0,
+             eos_a=CS_RESCALED["eos_a"], eos_b=CS_RESCALED["eos_b"], eos_R=CS_RESCALED["eos_R"],
+             eos_T=0.7 * CS_RESCALED["Tc"], rho_ref=(rl, rho2_liq),
+             n_species=3, idx_A=IDX_DERIVED, idx_B=0, idx_E=1, idx_F=2,
+             J0=_pad([1.0 / 3.0] * 3), tau_g=_pad([0.8] * 3, 1.0), conc_ref=_pad([0.0] * 3),
+             k1=k1, k3=k3, k2=k2, k4=k4, C_F_sat=0.0,
+             gas_yield=0.5, inv_M_C=1.0, c_total_per_rho1=1.0 / rl,
+             Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=seed,
+             rho_in_liq=(1.01 * rl, rho2_liq), rho_in_gas=(rg, rho2_gas),
+             rho_out=(rl, rho2_liq), inlet_period_liq=int(slug[0]), inlet_period_gas=int(slug[1]),
+             conc_in=_pad([0.0] * 3))
+    conc = np.zeros((3, ny, nx))
+    return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
