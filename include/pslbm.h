@@ -1,0 +1,185 @@
+/*
+ * pslbm.h -- C ABI of the GB300 (sm_103a) library for the pore-scale
+ * two-phase multi-mixture reactive lattice Boltzmann method of
+ * Chen, Kang, Tang, Robinson, He, Tao (arXiv 1410.3464).
+ *
+ * One time step (pslbm_step) advances, on the GPU, for every lattice node:
+ *   - the pseudo-potentials psi_1 (C-S EOS, Eqs. 12-13) and phi_1, phi_2
+ *     (Eq. 15), the Shan-Chen cohesion, inter-component and adhesion forces
+ *     (Eqs. 11, 14, 16) and the velocities of Eqs. 17-19;
+ *   - the D2Q9 BGK collide-stream of the liquid and gas components with the
+ *     reaction source omega_a S_sigma (Eqs. 6-8, 27) and halfway bounce-back;
+ *   - liquid/gas marking against half the maximum liquid-component density
+ *     (Section 4.5) with the concentration amendment at changed nodes;
+ *   - the D2Q5 collide-stream of every transported solute in the liquid phase
+ *     with homogeneous sources (Eqs. 20-24, 26, 28), no-flux liquid-gas links
+ *     and reactive liquid-solid links (Eqs. 29-31);
+ *   - the volume-of-pixel update of the solid volumes (Eqs. 32-35) and the
+ *     status changes solid<->liquid with their amendment (Section 4.7, Steps 4-5).
+ *
+ * Conventions
+ *   - Every call returns a pslbm_status; PSLBM_OK is 0, errors are negative.
+ *   - Host arrays are row-major [ny][nx] (index y*nx + x), borrowed for the
+ *     duration of the call and copied; outputs go to caller-owned host buffers.
+ *   - Errors are sticky per handle: after a device error every call on the
+ *     handle returns it; pslbm_last_error() gives a message.  pslbm_destroy()
+ *     is always safe.
+ *   - Work is queued on the library stream (pslbm_get_stream / pslbm_set_stream)
+ *     and is asynchronous; pslbm_read_fields and pslbm_sync synchronise it.
+ *   - Calls on one handle are not thread-safe; distinct handles may be used
+ *     from distinct threads only if they are not in the same batch.
+ */
+#ifndef PSLBM_H
+#define PSLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pslbm_s* pslbm_t;          /* one simulation, owned by the library */
+typedef struct pslbm_batch_s* pslbm_batch_t; /* a group of simulations stepped together */
+
+typedef enum {
+    PSLBM_OK = 0,
+    PSLBM_ERR_PARAM = -1,       /* invalid argument or parameter set */
+    PSLBM_ERR_OOM = -2,         /* device or host allocation failed (nothing leaked) */
+    PSLBM_ERR_CUDA = -3,        /* CUDA runtime error (message in pslbm_last_error) */
+    PSLBM_ERR_NONFINITE = -4,   /* a density became NaN/Inf on the device */
+    PSLBM_ERR_EOS_DOMAIN = -5,  /* Eq. 13 square-root argument negative (rho_1 out of the EOS domain) */
+    PSLBM_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+    PSLBM_ERR_STATE = -7,       /* call not valid in the handle's current state */
+    PSLBM_ERR_NODEVICE = -8     /* no CUDA device, or not an sm_103 device */
+} pslbm_status;
+
+typedef enum {
+    PSLBM_FP64 = 0,              /* populations stored and computed in FP64 */
+    PSLBM_FP32 = 1,              /* FP32 compute, populations stored as f - w_a rho_ref (shifted) */
+    PSLBM_FP32_SOLUTE_F16 = 2,   /* as FP32, solute populations stored in IEEE half */
+    PSLBM_FP32_SOLUTE_BF16 = 3   /* as FP32, solute populations stored in bfloat16 */
+} pslbm_precision;
+
+/* Node types (Fig. 2: liquid, gas, solid D(s), solid F(s); plus inert walls and
+ * reservoir nodes that push a fixed equilibrium state into their neighbours). */
+enum {
+    PSLBM_LIQUID = 0, PSLBM_GAS = 1, PSLBM_SOLID_D = 2, PSLBM_SOLID_F = 3,
+    PSLBM_WALL = 4, PSLBM_INLET = 5, PSLBM_OUTLET = 6
+};
+
+#define PSLBM_MAX_SPECIES 4
+#define PSLBM_IDX_ABSENT (-1)
+#define PSLBM_IDX_DERIVED (-2)
+
+/* Parameter block.  struct_size must be sizeof(pslbm_params). */
+typedef struct {
+    uint32_t struct_size;
+    int32_t nx, ny;                /* lattice size, nx, ny >= 1, nx*ny < 2^31 */
+    int32_t periodic_x, periodic_y;/* 1: periodic axis; 0: outside the edge acts as a wall */
+    int32_t precision;             /* pslbm_precision */
+    /* fluid: Eqs. 6-19 */
+    double tau[2];                 /* BGK relaxation times (> 0.5), liquid and gas component */
+    double G11, G12, G21;          /* Eq. 11 cohesion (G22 = 0), Eq. 14 cross interactions */
+    double a0, rho10, rho20;       /* Eq. 15 constants */
+    double w_adh[2];               /* Eq. 16 fluid-solid interaction strengths */
+    double eos_a, eos_b, eos_R, eos_T; /* Eq. 12 Carnahan-Starling constants and temperature */
+    double body_force[2];          /* optional uniform acceleration (x, y) */
+    double rho_ref[2];             /* reference densities: FP32 population shift and the
+                                      fill density of a refilled node with no fluid neighbour */
+    /* solutes: Eqs. 20-24 */
+    int32_t n_species;             /* transported species, 0..PSLBM_MAX_SPECIES */
+    int32_t idx_A, idx_B, idx_E, idx_F; /* species index of A, B, E, F; -1 absent; A may be -2 (derived) */
+    double J0[PSLBM_MAX_SPECIES];  /* rest fractions (Eq. 22), 0 <= J0 < 1 */
+    double tau_g[PSLBM_MAX_SPECIES];  /* relaxation times (> 0.5) */
+    double conc_ref[PSLBM_MAX_SPECIES]; /* FP32/16-bit solute population shift */
+    /* reactions: Eqs. 1-5, 27-31 */
+    double k1, inv_Keq, k3;        /* homogeneous R1 = k1 (C_A - inv_Keq C_B sqrt(C_C)), R3 = k3 C_B C_E */
+    double k2, k4, C_F_sat;        /* heterogeneous R2 = k2 C_B at D(s), R4 = k4 (C_F - C_F_sat) at D(s)/F(s) */
+    double gas_yield;              /* Eq. 27: S_2 = -S_1 = gas_yield * R1 (0.5 M_C) */
+    double inv_M_C;                /* C_C = rho_2 * inv_M_C */
+    double c_total_per_rho1;       /* derived A: C_A = max(0, c_total_per_rho1 rho_1 - sum_k C_k) */
+    /* volume of pixel: Eqs. 32-35 */
+    double Vbar_D, Vbar_F;         /* molar volumes of D(s), F(s) */
+    double V_split;                /* overflow threshold of V_D + V_F (> 1) */
+    uint64_t seed;                 /* seed of the overflow-neighbour choice (SplitMix64) */
+    /* reservoir nodes */
+    double rho_in_liq[2], rho_in_gas[2]; /* inlet densities during liquid / gas slugs */
+    double rho_out[2];             /* outlet densities */
+    int32_t inlet_period_liq, inlet_period_gas; /* slug lengths in steps (gas 0: always liquid) */
+    double conc_in[PSLBM_MAX_SPECIES];  /* inlet concentrations */
+} pslbm_params;
+
+/* Field selectors for pslbm_read_fields; each selected field has its own
+ * caller-owned host buffer in `out`, in the order of the bits below.  Doubles
+ * unless noted; fields are 0 where they are not defined. */
+enum {
+    PSLBM_F_RHO1 = 1u << 0,      /* [ny*nx] liquid-component density (fluid nodes) */
+    PSLBM_F_RHO2 = 1u << 1,      /* [ny*nx] gas-component density (fluid nodes) */
+    PSLBM_F_UX = 1u << 2,        /* [ny*nx] physical velocity u_r of Eq. 19, x (fluid nodes) */
+    PSLBM_F_UY = 1u << 3,        /* [ny*nx] u_r, y */
+    PSLBM_F_CONC = 1u << 4,      /* [n_species*ny*nx] concentrations (liquid nodes) */
+    PSLBM_F_TYPE = 1u << 5,      /* [ny*nx] uint8 node types */
+    PSLBM_F_VOL = 1u << 6,       /* [2*ny*nx] V_D then V_F */
+    PSLBM_F_BUDGET = 1u << 7     /* [6 + n_species]: max rho1, sum rho1, sum rho2 (fluid),
+                                    sum C_k (liquid), sum V_D, sum V_F, step count (as double) */
+};
+
+/* Library stream: all device work of the library is ordered on it.  The
+ * getter returns a cudaStream_t as void*.  set_stream(NULL) restores the
+ * library's own stream; the caller keeps ownership of a stream it passes. */
+void* pslbm_get_stream(void);
+pslbm_status pslbm_set_stream(void* cuda_stream);
+
+/* Create a simulation.
+ *   mask      [ny*nx] node types (required).
+ *   rho1,rho2 [ny*nx] initial densities at fluid nodes (required); populations
+ *             start at the rest equilibrium of Eq. 8.
+ *   conc      [n_species*ny*nx] initial concentrations at liquid nodes, or NULL (0);
+ *             solute populations start at J_a C (Eq. 21 at rest).
+ *   vol       [2*ny*nx] initial V_D, V_F, or NULL (1 at SOLID_D / SOLID_F nodes).
+ *   p         parameters (validated: PSLBM_ERR_PARAM on invalid values, incl.
+ *             tau <= 0.5, k >= (1 - J0)/2 for a reactive species, bad indices).
+ * On success *out holds a new handle; on failure *out is NULL and nothing leaks.
+ * The initial liquid threshold is half the maximum initial rho1 over fluid nodes. */
+pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double* rho2,
+                          const double* conc, const double* vol,
+                          const pslbm_params* p, pslbm_t* out);
+
+/* Advance n >= 0 time steps (asynchronous; replays a captured CUDA graph). */
+pslbm_status pslbm_step(pslbm_t h, int64_t n);
+
+/* Wait for queued work and report any device-side status (non-finite
+ * density, EOS domain) as an error. */
+pslbm_status pslbm_sync(pslbm_t h);
+
+/* Copy the selected fields (bit mask of PSLBM_F_*) to host buffers out[i]
+ * (one per selected field, in bit order).  Synchronises the stream. */
+pslbm_status pslbm_read_fields(pslbm_t h, uint32_t fields, void* const* out);
+
+/* Number of steps taken and lattice size. */
+pslbm_status pslbm_info(pslbm_t h, int64_t* steps, int32_t* nx, int32_t* ny, int32_t* n_species);
+
+/* Device bytes held by the handle. */
+pslbm_status pslbm_device_bytes(pslbm_t h, uint64_t* bytes);
+
+/* Release all resources of the handle (safe on NULL and on failed handles). */
+pslbm_status pslbm_destroy(pslbm_t h);
+
+/* Last error message of the handle (or of the library when h is NULL). */
+const char* pslbm_last_error(pslbm_t h);
+
+/* ---------------------------------------------------------------- batching
+ * A batch steps several simulations (same precision and species count) in
+ * one launch per kernel over a packed list of tiles of all members.  The
+ * members stay valid handles; they must not be stepped on their own while
+ * the batch exists.  tile_x, tile_y choose the tile shape (0: automatic). */
+pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_x, int32_t tile_y,
+                                pslbm_batch_t* out);
+pslbm_status pslbm_batch_step(pslbm_batch_t b, int64_t n);
+pslbm_status pslbm_batch_sync(pslbm_batch_t b);
+pslbm_status pslbm_batch_destroy(pslbm_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSLBM_H */

@@ -459,6 +459,7 @@ class Lattice:
 
         # 2. concentration amendment at marking changes
         C = np.stack([self._conc(self.g[k]) for k in range(ns)]) if ns else np.zeros((0, ny, nx))
+        C_pre = C.copy()
         g = self.g.copy()
         if ns:
             vanish = np.argwhere(old_liq & ~liq_new)
@@ -575,7 +576,9 @@ class Lattice:
             Cres = np.zeros((ns, ny, nx))
             for k in range(ns):
                 cin = p["conc_in"][k]
-                cl = np.where(liq_new, C[k], 0.0)
+                # outlet: concentration of the node upstream along x at the
+                # start of the step when it is liquid, else 0
+                cl = np.where(liq_new, C_pre[k], 0.0)
                 Cres[k] = np.where(inlet, cin, np.where(outlet, self.nb(cl, -1, 0, 0.0), 0.0))
             k2, k4, Csat = p["k2"], p["k4"], p["C_F_sat"]
             for a in range(5):

@@ -1,0 +1,204 @@
+// Initialisation, field read-out and deterministic budget reduction.
+#pragma once
+#include "device.cuh"
+
+namespace pslbm {
+
+// Rest equilibrium (Eq. 8 at u = 0, Eq. 21 at u = 0) from initial fields.
+template <class TF, class TG, class R, int NS>
+__global__ void k_init(DevInst* __restrict__ Ip, const uint8_t* __restrict__ mask, const double* __restrict__ rho1,
+                       const double* __restrict__ rho2, const double* __restrict__ conc) {
+  const DevParams& P = Ip->P;
+  const long long N = Ip->N;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < N;
+       node += (long long)gridDim.x * blockDim.x) {
+    const uint8_t t = mask[node] & T_MASK;
+    Ip->type[0][node] = t;
+    Ip->type[1][node] = t;
+    TF* F = (TF*)Ip->f[0];
+    TG* G = (TG*)Ip->g[0];
+    const bool fl = is_fluid(t);
+    const R r1 = fl ? R(rho1[node]) : R(0), r2 = fl ? R(rho2[node]) : R(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const R w = w9<R>(a);
+      st<TF, R>(F + a * N + node, fl ? w * r1 - w * R(P.shift_f[0]) : R(0));
+      st<TF, R>(F + (9 + a) * N + node, fl ? w * r2 - w * R(P.shift_f[1]) : R(0));
+    }
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const R c = (t == T_LIQUID && conc) ? R(conc[k * N + node]) : R(0);
+      const R J0 = R(P.J0[k]), Ja = (R(1) - J0) / R(4);
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        const R ja = a == 0 ? J0 : Ja;
+        st<TG, R>(G + ((long long)k * 5 + a) * N + node, ja * c - ja * R(P.shift_c[k]));
+      }
+    }
+  }
+}
+
+// Observable fields of the current state: rho_1, rho_2, u_r (Eq. 19) at fluid
+// nodes, C_k at liquid nodes, node types.  Forces are recomputed from the
+// neighbours' densities exactly as in the bulk kernel.
+template <class TF, class TG, class R, int NS>
+__global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_rho1, double* __restrict__ o_rho2,
+                         double* __restrict__ o_ux, double* __restrict__ o_uy, double* __restrict__ o_conc,
+                         uint8_t* __restrict__ o_type) {
+  const DevParams& P = Ip->P;
+  const long long N = Ip->N;
+  const unsigned long long step = Ip->scal[S_STEP];
+  const int cur = int(step & 1ULL);
+  const TF* F = (const TF*)Ip->f[cur];
+  const TG* G = (const TG*)Ip->g[cur];
+  const uint8_t* T = Ip->type[cur];
+  unsigned status = 0;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < N;
+       node += (long long)gridDim.x * blockDim.x) {
+    const uint8_t t = T[node] & T_MASK;
+    o_type[node] = t;
+    double r1o = 0, r2o = 0, uxo = 0, uyo = 0;
+    const int x = int(node % P.nx), y = int(node / P.nx);
+    if (is_fluid(t)) {
+      R f1[9], f2[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        f1[a] = ldc<R>(F + a * N + node);
+        f2[a] = ldc<R>(F + (9 + a) * N + node);
+      }
+      R d1 = f1[0], d2 = f2[0];
+#pragma unroll
+      for (int a = 1; a < 9; ++a) { d1 += f1[a]; d2 += f2[a]; }
+      const R rho1 = R(P.shift_f[0]) + d1, rho2 = R(P.shift_f[1]) + d2;
+      const R j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
+      const R j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
+      const R j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
+      const R j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
+      R psc, p1c, p2c;
+      potentials<R>(P, rho1, rho2, psc, p1c, p2c, status);
+      R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
+#pragma unroll
+      for (int a = 1; a < 9; ++a) {
+        int xn, yn;
+        const bool in = nbr(P, x, y, EX(a), EY(a), xn, yn);
+        const long long nn = (long long)yn * P.nx + xn;
+        const uint8_t tn = in ? (T[nn] & T_MASK) : T_WALL;
+        R ps = psc, q1 = p1c, q2 = p2c, sv = R(1);
+        if (is_live(tn)) {
+          R a1, a2;
+          if (is_fluid(tn)) {
+            a1 = R(P.shift_f[0]) + density_shifted<R>(F, N, nn);
+            a2 = R(P.shift_f[1]) + density_shifted<R>(F + 9 * N, N, nn);
+          } else {
+            double u, v;
+            reservoir_rho(P, tn, step, u, v);
+            a1 = R(u);
+            a2 = R(v);
+          }
+          potentials<R>(P, a1, a2, ps, q1, q2, status);
+          sv = R(0);
+        }
+        const R w = wf<R>(a);
+        const R vp = w * ps, v2 = w * q2, v1 = w * q1, vs = w * sv;
+        if (EX(a) > 0) { spx += vp; s2x += v2; s1x += v1; ssx += vs; }
+        if (EX(a) < 0) { spx -= vp; s2x -= v2; s1x -= v1; ssx -= vs; }
+        if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
+        if (EY(a) < 0) { spy -= vp; s2y -= v2; s1y -= v1; ssy -= vs; }
+      }
+      const R G11 = R(P.G11), G12 = R(P.G12), G21 = R(P.G21), w1 = R(P.w_adh[0]), w2 = R(P.w_adh[1]);
+      const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * R(P.gx);
+      const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * R(P.gy);
+      const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * R(P.gx);
+      const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * R(P.gy);
+      const R rt = rho1 + rho2;
+      r1o = double(rho1);
+      r2o = double(rho2);
+      uxo = double((j1x + j2x + R(0.5) * (F1x + F2x)) / rt);
+      uyo = double((j1y + j2y + R(0.5) * (F1y + F2y)) / rt);
+    }
+    if (o_rho1) o_rho1[node] = r1o;
+    if (o_rho2) o_rho2[node] = r2o;
+    if (o_ux) o_ux[node] = uxo;
+    if (o_uy) o_uy[node] = uyo;
+    if (o_conc) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        double c = 0.0;
+        if (t == T_LIQUID) {
+          const TG* gk = G + (long long)k * 5 * N;
+          R s = ldc<R>(gk + node);
+#pragma unroll
+          for (int a = 1; a < 5; ++a) s += ldc<R>(gk + a * N + node);
+          c = double(R(P.shift_c[k]) + s);
+        }
+        o_conc[k * N + node] = c;
+      }
+    }
+  }
+}
+
+// Budget partials: per block [max rho1, sum rho1, sum rho2, sum C_k (k < NS), sum V_D, sum V_F].
+// Each block covers a fixed contiguous range and reduces in a fixed tree, so
+// the result is independent of scheduling.
+
+template <class TF, class TG, class R, int NS>
+__global__ void __launch_bounds__(BUD_THREADS) k_budget_partial(const DevInst* __restrict__ Ip,
+                                                                 double* __restrict__ part) {
+  const DevParams& P = Ip->P;
+  const long long N = Ip->N;
+  const int cur = int(Ip->scal[S_STEP] & 1ULL);
+  const TF* F = (const TF*)Ip->f[cur];
+  const TG* G = (const TG*)Ip->g[cur];
+  const uint8_t* T = Ip->type[cur];
+  const long long per = (N + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per, hi = min(N, lo + per);
+  double acc[NBUD];
+  acc[0] = -1.0 / 0.0;
+#pragma unroll
+  for (int i = 1; i < NBUD; ++i) acc[i] = 0.0;
+  for (long long node = lo + threadIdx.x; node < hi; node += blockDim.x) {
+    const uint8_t t = T[node] & T_MASK;
+    if (is_fluid(t)) {
+      const double r1 = double(R(P.shift_f[0]) + density_c<R>(F, N, node));
+      const double r2 = double(R(P.shift_f[1]) + density_c<R>(F + 9 * N, N, node));
+      acc[0] = fmax(acc[0], r1);
+      acc[1] += r1;
+      acc[2] += r2;
+    }
+    if (t == T_LIQUID) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const TG* gk = G + (long long)k * 5 * N;
+        R s = ldc<R>(gk + node);
+#pragma unroll
+        for (int a = 1; a < 5; ++a) s += ldc<R>(gk + a * N + node);
+        acc[3 + k] += double(R(P.shift_c[k]) + s);
+      }
+    }
+    acc[3 + MAXS] += Ip->V[node];
+    acc[4 + MAXS] += Ip->V[N + node];
+  }
+  __shared__ double sh[BUD_THREADS];
+  for (int i = 0; i < NBUD; ++i) {
+    sh[threadIdx.x] = acc[i];
+    __syncthreads();
+    for (int s = BUD_THREADS / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] = (i == 0) ? fmax(sh[threadIdx.x], sh[threadIdx.x + s])
+                                                      : sh[threadIdx.x] + sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x * NBUD + i] = sh[0];
+    __syncthreads();
+  }
+}
+
+static __global__ void k_budget_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < NBUD; ++i) {
+    double v = (i == 0) ? -1.0 / 0.0 : 0.0;
+    for (int b = 0; b < nblocks; ++b) v = (i == 0) ? fmax(v, part[b * NBUD + i]) : v + part[b * NBUD + i];
+    out[i] = v;
+  }
+}
+
+}  // namespace pslbm

@@ -1,0 +1,235 @@
+// Device-side data structures and per-node helpers of the reactive two-phase
+// LBM (Chen, Kang et al., arXiv 1410.3464, Sections 3-4).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+namespace pslbm {
+
+constexpr int MAXS = 4;
+constexpr uint8_t T_LIQUID = 0, T_GAS = 1, T_SOLID_D = 2, T_SOLID_F = 3, T_WALL = 4, T_INLET = 5,
+                  T_OUTLET = 6;
+constexpr uint8_t T_MASK = 0x0F;     // low nibble: node type
+constexpr uint8_t T_NEW = 0x40;      // flag set by the amendment kernel: solid -> liquid this step
+constexpr uint8_t T_VANISH = 0x80;   // flag: liquid -> solid this step
+
+// Tile shape of the bulk kernels (one thread per interior node).
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int EXT_X = TX + 2;
+constexpr int EXT_Y = TY + 2;
+constexpr int EXT = EXT_X * EXT_Y;
+constexpr int RING = EXT - TX * TY;
+constexpr int NTHREADS = TX * TY;
+
+// Per-instance scalar slots (unsigned long long each).
+enum {
+  S_STEP = 0,      // steps taken
+  S_MAX0 = 1,      // ordered-encoded max rho_1, slot for even steps
+  S_MAX1 = 2,      // slot for odd steps
+  S_STATUS = 3,    // error bits
+  S_NEVENT = 4,    // events recorded by the VOP kernel this step
+  S_DONE = 5,      // tiles of the VOP kernel finished this step
+  S_NSCAL = 8
+};
+enum { ST_NONFINITE = 1, ST_EOS = 2, ST_EVOVERFLOW = 4 };
+
+// Budget reduction: [max rho1, sum rho1, sum rho2, sum C_k (MAXS), sum V_D, sum V_F].
+constexpr int NBUD = 5 + MAXS;
+constexpr int BUD_BLOCKS = 512;
+constexpr int BUD_THREADS = 256;
+
+// Event codes written by the VOP kernel.
+enum { EV_NONE = 0, EV_DISSOLVE = 1, EV_OVERFLOW = 2 };   // overflow: code | (dir << 4)
+
+struct DevParams {
+  int nx, ny, px, py, ns;
+  int iA, iB, iE, iF;
+  int per_liq, per_gas;
+  double tau[2], G11, G12, G21, a0, rho10, rho20, w_adh[2];
+  double eos_a, eos_b, eos_R, eos_T;
+  double gx, gy;
+  double shift_f[2];       // population shift rho_ref (0 in FP64 storage)
+  double rho_fill[2];      // density of a refilled node without fluid neighbours
+  double J0[MAXS], tau_g[MAXS], shift_c[MAXS];
+  double k1, inv_Keq, k3, k2, k4, C_F_sat, gas_yield, inv_M_C, c_total_per_rho1;
+  double Vbar_D, Vbar_F, V_split;
+  unsigned long long seed;
+  double rho_in_liq[2], rho_in_gas[2], rho_out[2];
+  double conc_in[MAXS];
+};
+
+struct DevInst {
+  DevParams P;
+  void* f[2];                 // [2][9][N] populations, ping-pong
+  void* g[2];                 // [ns][5][N] solute populations, ping-pong
+  uint8_t* type[2];           // [N] node types, ping-pong
+  double* V;                  // [2][N] V_D, V_F
+  double* q;                  // [2][4][N] link fluxes of B and F toward a mineral (direction 1..4)
+  uint8_t* evt;               // [N] VOP events (zero except during a step)
+  double* xs;                 // [N] overflow excess of an event node
+  int* evlist;                // [evcap] event node indices
+  int* claim;                 // [N] zero except while the amendment kernel runs
+  unsigned long long* scal;   // [S_NSCAL]
+  long long N;
+  int evcap;
+  int ntiles;
+};
+
+struct Tile {
+  int inst, x0, y0, pad;
+};
+
+// D2Q9 velocity set of Eq. 7 (the D2Q5 set is directions 0-4).
+__host__ __device__ constexpr int ex_(int a) {
+  return (a == 1 || a == 5 || a == 8) ? 1 : (a == 3 || a == 6 || a == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey_(int a) {
+  return (a == 2 || a == 5 || a == 6) ? 1 : (a == 4 || a == 7 || a == 8) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp_(int a) {
+  return a == 0 ? 0 : a == 1 ? 3 : a == 2 ? 4 : a == 3 ? 1 : a == 4 ? 2 : a == 5 ? 7 : a == 6 ? 8 : a == 7 ? 5 : 6;
+}
+#define EX(a) ex_(a)
+#define EY(a) ey_(a)
+#define OPP(a) opp_(a)
+
+template <class R> __device__ __forceinline__ R w9(int a) {
+  return a == 0 ? R(4.0 / 9.0) : (a < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+// interaction weights w(|e|^2): 1/9 axis, 1/36 diagonal (sum w e_x^2 = c_s^2)
+template <class R> __device__ __forceinline__ R wf(int a) {
+  return a == 0 ? R(0) : (a < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+
+__device__ __forceinline__ bool is_fluid(uint8_t t) { return t <= T_GAS; }
+__device__ __forceinline__ bool is_res(uint8_t t) { return t == T_INLET || t == T_OUTLET; }
+__device__ __forceinline__ bool is_live(uint8_t t) { return t <= T_GAS || t == T_INLET || t == T_OUTLET; }
+__device__ __forceinline__ bool is_mineral(uint8_t t) { return t == T_SOLID_D || t == T_SOLID_F; }
+
+// Storage conversion.
+template <class T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class R, class T> __device__ __forceinline__ R ld(const T* p) { return R(to_f<T>(__ldg(p))); }
+template <> __device__ __forceinline__ double ld<double, double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld<float, float>(const float* p) { return __ldg(p); }
+template <class T, class R> __device__ __forceinline__ void st(T* p, R v);
+template <> __device__ __forceinline__ void st<double, double>(double* p, double v) { *p = v; }
+template <> __device__ __forceinline__ void st<float, float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void st<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
+template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+// plain (coherent) loads for data written earlier in the same kernel sequence
+template <class R, class T> __device__ __forceinline__ R ldc(const T* p) { return R(to_f<T>(*p)); }
+template <> __device__ __forceinline__ double ldc<double, double>(const double* p) { return *p; }
+template <> __device__ __forceinline__ float ldc<float, float>(const float* p) { return *p; }
+
+// Neighbour coordinate with periodic wrap; false outside a non-periodic edge.
+__device__ __forceinline__ bool nbr(const DevParams& P, int x, int y, int dx, int dy, int& xn, int& yn) {
+  xn = x + dx;
+  yn = y + dy;
+  if (xn < 0 || xn >= P.nx) {
+    if (!P.px) return false;
+    xn %= P.nx;
+    if (xn < 0) xn += P.nx;
+  }
+  if (yn < 0 || yn >= P.ny) {
+    if (!P.py) return false;
+    yn %= P.ny;
+    if (yn < 0) yn += P.ny;
+  }
+  return true;
+}
+
+// Order-preserving map of doubles to unsigned 64-bit (for atomicMax).
+__device__ __forceinline__ unsigned long long ord_enc(double v) {
+  unsigned long long b = __double_as_longlong(v);
+  return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+__host__ __device__ inline double ord_dec(unsigned long long e) {
+  unsigned long long b = (e & 0x8000000000000000ULL) ? (e & 0x7FFFFFFFFFFFFFFFULL) : ~e;
+  union { unsigned long long u; double d; } c;
+  c.u = b;
+  return c.d;
+}
+
+// Eq. 9a with the population shift: delta rho summed in direction order.
+template <class R, class TF>
+__device__ __forceinline__ R density_shifted(const TF* f, long long N, long long node) {
+  R s = ld<R>(f + node);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) s += ld<R>(f + a * N + node);
+  return s;
+}
+
+// Same sum through plain (coherent) loads, for data written by an earlier kernel
+// of the same step.
+template <class R, class TF>
+__device__ __forceinline__ R density_c(const TF* f, long long N, long long node) {
+  R s = ldc<R>(f + node);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) s += ldc<R>(f + a * N + node);
+  return s;
+}
+
+// Reservoir densities at step t (inlet slugs alternate liquid and gas).
+__device__ __forceinline__ void reservoir_rho(const DevParams& P, uint8_t t, unsigned long long step, double& r1,
+                                              double& r2) {
+  if (t == T_INLET) {
+    bool liq = P.per_gas <= 0 || (long long)(step % (unsigned long long)(P.per_liq + P.per_gas)) < P.per_liq;
+    r1 = liq ? P.rho_in_liq[0] : P.rho_in_gas[0];
+    r2 = liq ? P.rho_in_liq[1] : P.rho_in_gas[1];
+  } else {
+    r1 = P.rho_out[0];
+    r2 = P.rho_out[1];
+  }
+}
+
+// Eq. 12 (C-S EOS) and the Eq. 13 square-root argument.
+template <class R> __device__ __forceinline__ R psi_arg(const DevParams& P, R rho) {
+  R eta = R(P.eos_b) * rho / R(4);
+  R om = R(1) - eta;
+  R p = rho * R(P.eos_R) * R(P.eos_T) * (R(1) + eta + eta * eta - eta * eta * eta) / (om * om * om) -
+        R(P.eos_a) * rho * rho;
+  return R(6) / R(P.G11) * (p - rho / R(3));
+}
+
+template <class R> __device__ __forceinline__ R rexp(R v);
+template <> __device__ __forceinline__ double rexp<double>(double v) { return exp(v); }
+template <> __device__ __forceinline__ float rexp<float>(float v) { return expf(v); }
+template <class R> __device__ __forceinline__ R rsqrt_(R v);
+template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqrtf(v); }
+
+// psi_1 (Eq. 13), phi_1, phi_2 (Eq. 15) of a live node; sets status bits on a bad argument.
+template <class R>
+__device__ __forceinline__ void potentials(const DevParams& P, R rho1, R rho2, R& psi, R& phi1, R& phi2,
+                                           unsigned& status) {
+  if (P.G11 != 0.0) {
+    R arg = psi_arg<R>(P, rho1);
+    if (!(arg >= R(0))) {
+      status |= (arg == arg) ? ST_EOS : ST_NONFINITE;
+      arg = R(0);
+    }
+    psi = rsqrt_<R>(arg);
+  } else {
+    psi = R(0);
+  }
+  phi1 = R(1) - rexp<R>(-rho2 / R(P.rho20));
+  phi2 = R(P.a0) - rexp<R>(-rho1 / R(P.rho10));
+}
+
+// SplitMix64 output for a given state (Steele, Lea, Flood 2014).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long s) {
+  unsigned long long z = s + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+}  // namespace pslbm

@@ -1,0 +1,6 @@
+// FP32 compute, FP32 shifted fluid populations, bfloat16 solute populations.
+#define KTF float
+#define KTG __nv_bfloat16
+#define KR float
+#define KNAME launchers_f32b
+#include "kernels_impl.cuh"

@@ -1,0 +1,52 @@
+// Explicit instantiation of the step kernels for one storage precision.
+// Included by one translation unit per precision with KTF (population
+// storage), KTG (solute storage), KR (compute type) and KNAME defined.
+#include "launch.h"
+#include "bulk.cuh"
+#include "interface.cuh"
+#include "aux.cuh"
+
+namespace pslbm {
+namespace {
+
+template <int NS>
+void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
+  if (ntiles <= 0) return;
+  k_bulk<KTF, KTG, KR, NS><<<ntiles, NTHREADS, 0, s>>>(tiles, ntiles, insts);
+}
+template <int NS>
+void amend_l(cudaStream_t s, int ninst, const DevInst* insts) {
+  if (ninst <= 0) return;
+  k_amend<KTF, KTG, KR, NS><<<ninst, NTHREADS, 0, s>>>(insts);
+}
+template <int NS>
+void init_l(cudaStream_t s, DevInst* I, const uint8_t* m, const double* r1, const double* r2, const double* c,
+            long long N) {
+  long long blocks = (N + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  k_init<KTF, KTG, KR, NS><<<(int)blocks, 256, 0, s>>>(I, m, r1, r2, c);
+}
+template <int NS>
+void fields_l(cudaStream_t s, const DevInst* I, long long N, double* r1, double* r2, double* ux, double* uy,
+              double* c, uint8_t* t) {
+  long long blocks = (N + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  k_fields<KTF, KTG, KR, NS><<<(int)blocks, 256, 0, s>>>(I, r1, r2, ux, uy, c, t);
+}
+template <int NS>
+void budget_l(cudaStream_t s, const DevInst* I, double* part, double* out) {
+  k_budget_partial<KTF, KTG, KR, NS><<<BUD_BLOCKS, BUD_THREADS, 0, s>>>(I, part);
+  k_budget_final<<<1, 32, 0, s>>>(part, BUD_BLOCKS, out);
+}
+
+template <int NS>
+constexpr Launchers make() {
+  return Launchers{&bulk_l<NS>, &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
+}
+const Launchers table[MAXS + 1] = {make<0>(), make<1>(), make<2>(), make<3>(), make<4>()};
+
+}  // namespace
+
+const Launchers* KNAME(int ns) { return (ns >= 0 && ns <= MAXS) ? &table[ns] : nullptr; }
+
+}  // namespace pslbm

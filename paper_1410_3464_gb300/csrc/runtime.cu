@@ -1,0 +1,684 @@
+// Host runtime behind the C ABI of include/pslbm.h: parameter validation,
+// device allocation of the structure-of-arrays state, tile lists, CUDA-graph
+// capture of whole steps, field read-out and batches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pslbm.h"
+#include "launch.h"
+
+using namespace pslbm;
+
+namespace {
+
+std::mutex g_mu;
+cudaStream_t g_own_stream = nullptr;
+cudaStream_t g_user_stream = nullptr;
+bool g_user_set = false;
+std::string g_lib_err;
+
+cudaStream_t lib_stream() {
+  if (g_user_set) return g_user_stream;
+  if (!g_own_stream) cudaStreamCreateWithFlags(&g_own_stream, cudaStreamNonBlocking);
+  return g_own_stream;
+}
+
+size_t fsize(int prec) { return prec == PSLBM_FP64 ? 8 : 4; }
+size_t gsize(int prec) { return prec == PSLBM_FP64 ? 8 : (prec == PSLBM_FP32 ? 4 : 2); }
+
+struct GraphCache {
+  std::map<int64_t, cudaGraphExec_t> exec;
+  void clear() {
+    for (auto& kv : exec) cudaGraphExecDestroy(kv.second);
+    exec.clear();
+  }
+};
+
+}  // namespace
+
+struct pslbm_s {
+  pslbm_params p{};
+  int prec = 0;
+  int ns = 0;
+  long long N = 0;
+  DevInst h{};                 // host copy of the device descriptor
+  DevInst* d = nullptr;        // device descriptor
+  Tile* tiles = nullptr;
+  int ntiles = 0;
+  std::vector<void*> allocs;
+  uint64_t bytes = 0;
+  double* rb = nullptr;        // read-back scratch
+  size_t rb_bytes = 0;
+  std::string err;
+  pslbm_status sticky = PSLBM_OK;
+  GraphCache graphs;
+  int in_batch = 0;
+  const Launchers* L = nullptr;
+};
+
+struct pslbm_batch_s {
+  std::vector<pslbm_t> members;
+  DevInst* d = nullptr;
+  Tile* tiles = nullptr;
+  int ntiles = 0;
+  GraphCache graphs;
+  const Launchers* L = nullptr;
+  std::string err;
+  pslbm_status sticky = PSLBM_OK;
+};
+
+namespace {
+
+pslbm_status fail(pslbm_t h, pslbm_status s, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (s == PSLBM_ERR_CUDA || s == PSLBM_ERR_NONFINITE || s == PSLBM_ERR_EOS_DOMAIN) h->sticky = s;
+  } else {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_lib_err = msg;
+  }
+  return s;
+}
+
+#define CK(h, call)                                                                                   \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(h, PSLBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+pslbm_status check_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return PSLBM_ERR_NODEVICE;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return PSLBM_ERR_NODEVICE;
+  if (!(prop.major == 10 && prop.minor == 3)) return PSLBM_ERR_NODEVICE;
+  return PSLBM_OK;
+}
+
+std::string validate(const pslbm_params* p) {
+  char buf[256];
+  if (!p) return "params is NULL";
+  if (p->struct_size != sizeof(pslbm_params)) {
+    snprintf(buf, sizeof buf, "struct_size %u != %zu", p->struct_size, sizeof(pslbm_params));
+    return buf;
+  }
+  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny >= (1LL << 31)) return "bad lattice size";
+  if (p->precision < 0 || p->precision > 3) return "bad precision";
+  for (int s = 0; s < 2; ++s)
+    if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) return "tau must be > 0.5";
+  if (p->n_species < 0 || p->n_species > PSLBM_MAX_SPECIES) return "n_species out of range";
+  if (p->precision >= 2 && p->n_species == 0) return "16-bit solute storage needs species";
+  const int ns = p->n_species;
+  auto okidx = [&](int i, bool allow_derived) {
+    return i == PSLBM_IDX_ABSENT || (i >= 0 && i < ns) || (allow_derived && i == PSLBM_IDX_DERIVED);
+  };
+  if (!okidx(p->idx_A, true) || !okidx(p->idx_B, false) || !okidx(p->idx_E, false) || !okidx(p->idx_F, false))
+    return "species index out of range";
+  {
+    int ids[4] = {p->idx_A, p->idx_B, p->idx_E, p->idx_F};
+    for (int i = 0; i < 4; ++i)
+      for (int j = i + 1; j < 4; ++j)
+        if (ids[i] >= 0 && ids[i] == ids[j]) return "two roles share one species index";
+  }
+  for (int k = 0; k < ns; ++k) {
+    if (!(p->J0[k] >= 0.0 && p->J0[k] < 1.0)) return "J0 must be in [0, 1)";
+    if (!(p->tau_g[k] > 0.5)) return "tau_g must be > 0.5";
+  }
+  if (p->G11 != 0.0 && !(p->eos_b > 0 && p->eos_R > 0 && p->eos_T > 0)) return "bad EOS constants";
+  if (!(p->rho10 != 0.0 && p->rho20 != 0.0)) return "rho10, rho20 must be nonzero";
+  // reactive link rule needs kappa = k / (2 J_w) < 1
+  if (p->idx_B >= 0 && p->k2 != 0.0 && !(p->k2 >= 0.0 && p->k2 < 0.5 * (1.0 - p->J0[p->idx_B])))
+    return "k2 must be in [0, (1 - J0_B)/2)";
+  if (p->idx_F >= 0 && p->k4 != 0.0 && !(p->k4 >= 0.0 && p->k4 < 0.5 * (1.0 - p->J0[p->idx_F])))
+    return "k4 must be in [0, (1 - J0_F)/2)";
+  if (!(p->V_split > 1.0)) return "V_split must be > 1";
+  if (p->inlet_period_liq < 0 || p->inlet_period_gas < 0 ||
+      (p->inlet_period_gas > 0 && p->inlet_period_liq + p->inlet_period_gas <= 0))
+    return "bad inlet periods";
+  return "";
+}
+
+DevParams to_dev(const pslbm_params* p) {
+  DevParams P{};
+  P.nx = p->nx;
+  P.ny = p->ny;
+  P.px = p->periodic_x ? 1 : 0;
+  P.py = p->periodic_y ? 1 : 0;
+  P.ns = p->n_species;
+  P.iA = p->idx_A;
+  P.iB = p->idx_B;
+  P.iE = p->idx_E;
+  P.iF = p->idx_F;
+  P.per_liq = p->inlet_period_liq;
+  P.per_gas = p->inlet_period_gas;
+  for (int s = 0; s < 2; ++s) {
+    P.tau[s] = p->tau[s];
+    P.w_adh[s] = p->w_adh[s];
+    P.shift_f[s] = p->precision == PSLBM_FP64 ? 0.0 : p->rho_ref[s];
+    P.rho_fill[s] = p->rho_ref[s];
+    P.rho_in_liq[s] = p->rho_in_liq[s];
+    P.rho_in_gas[s] = p->rho_in_gas[s];
+    P.rho_out[s] = p->rho_out[s];
+  }
+  P.G11 = p->G11;
+  P.G12 = p->G12;
+  P.G21 = p->G21;
+  P.a0 = p->a0;
+  P.rho10 = p->rho10;
+  P.rho20 = p->rho20;
+  P.eos_a = p->eos_a;
+  P.eos_b = p->eos_b;
+  P.eos_R = p->eos_R;
+  P.eos_T = p->eos_T;
+  P.gx = p->body_force[0];
+  P.gy = p->body_force[1];
+  for (int k = 0; k < MAXS; ++k) {
+    P.J0[k] = p->J0[k];
+    P.tau_g[k] = k < p->n_species ? p->tau_g[k] : 1.0;
+    P.shift_c[k] = p->precision == PSLBM_FP64 ? 0.0 : p->conc_ref[k];
+    P.conc_in[k] = p->conc_in[k];
+  }
+  P.k1 = p->k1;
+  P.inv_Keq = p->inv_Keq;
+  P.k3 = p->k3;
+  P.k2 = p->k2;
+  P.k4 = p->k4;
+  P.C_F_sat = p->C_F_sat;
+  P.gas_yield = p->gas_yield;
+  P.inv_M_C = p->inv_M_C;
+  P.c_total_per_rho1 = p->c_total_per_rho1;
+  P.Vbar_D = p->Vbar_D;
+  P.Vbar_F = p->Vbar_F;
+  P.V_split = p->V_split;
+  P.seed = p->seed;
+  return P;
+}
+
+std::vector<Tile> make_tiles(int inst, int nx, int ny) {
+  std::vector<Tile> t;
+  for (int y0 = 0; y0 < ny; y0 += TY)
+    for (int x0 = 0; x0 < nx; x0 += TX) t.push_back(Tile{inst, x0, y0, 0});
+  return t;
+}
+
+pslbm_status dalloc(pslbm_t h, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(h, e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*ptr);
+  h->bytes += bytes;
+  return PSLBM_OK;
+}
+
+void free_all(pslbm_t h) {
+  h->graphs.clear();
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+// Enqueue n steps of the kernels over a tile list.
+void enqueue_steps(cudaStream_t s, const Launchers* L, const Tile* tiles, int ntiles, const DevInst* d, int ninst,
+                   int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    L->bulk(s, tiles, ntiles, d);
+    launch_vop(s, tiles, ntiles, d);
+    L->amend(s, ninst, d);
+  }
+}
+
+// Run n steps, replaying captured graphs of up to 32 steps.
+pslbm_status run_steps(GraphCache& gc, const Launchers* L, const Tile* tiles, int ntiles, const DevInst* d,
+                       int ninst, int64_t n, std::string& err) {
+  cudaStream_t s = lib_stream();
+  const int64_t K = 32;
+  while (n > 0) {
+    const int64_t k = n >= K ? K : n;
+    auto it = gc.exec.find(k);
+    if (it == gc.exec.end()) {
+      cudaGraph_t g;
+      cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+        return PSLBM_ERR_CUDA;
+      }
+      enqueue_steps(s, L, tiles, ntiles, d, ninst, k);
+      e = cudaStreamEndCapture(s, &g);
+      if (e != cudaSuccess) {
+        err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+        return PSLBM_ERR_CUDA;
+      }
+      cudaGraphExec_t ex;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        return PSLBM_ERR_CUDA;
+      }
+      it = gc.exec.emplace(k, ex).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, s);
+    if (e != cudaSuccess) {
+      err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+      return PSLBM_ERR_CUDA;
+    }
+    n -= k;
+  }
+  return PSLBM_OK;
+}
+
+pslbm_status device_status(pslbm_t h) {
+  unsigned long long st = 0;
+  CK(h, cudaMemcpyAsync(&st, h->h.scal + S_STATUS, sizeof st, cudaMemcpyDeviceToHost, lib_stream()));
+  CK(h, cudaStreamSynchronize(lib_stream()));
+  if (st & ST_NONFINITE) return fail(h, PSLBM_ERR_NONFINITE, "non-finite density on the device");
+  if (st & ST_EOS) return fail(h, PSLBM_ERR_EOS_DOMAIN, "Eq. 13 square-root argument negative (rho_1 outside the EOS domain)");
+  return PSLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void* pslbm_get_stream(void) { return (void*)lib_stream(); }
+
+pslbm_status pslbm_set_stream(void* s) {
+  g_user_set = s != nullptr;
+  g_user_stream = (cudaStream_t)s;
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double* rho2, const double* conc,
+                          const double* vol, const pslbm_params* p, pslbm_t* out) {
+  if (!out) return fail(nullptr, PSLBM_ERR_PARAM, "out is NULL");
+  *out = nullptr;
+  if (!mask || !rho1 || !rho2) return fail(nullptr, PSLBM_ERR_PARAM, "mask, rho1 and rho2 are required");
+  std::string v = validate(p);
+  if (!v.empty()) return fail(nullptr, PSLBM_ERR_PARAM, v);
+  if (check_device() != PSLBM_OK) return fail(nullptr, PSLBM_ERR_NODEVICE, "no sm_103 CUDA device");
+  const int ns = p->n_species;
+  const Launchers* L = launchers(p->precision, ns);
+  if (!L) return fail(nullptr, PSLBM_ERR_PARAM, "no kernels for this precision / species count");
+
+  pslbm_t h = new (std::nothrow) pslbm_s();
+  if (!h) return fail(nullptr, PSLBM_ERR_OOM, "host allocation failed");
+  h->p = *p;
+  h->prec = p->precision;
+  h->ns = ns;
+  h->L = L;
+  const long long N = (long long)p->nx * p->ny;
+  h->N = N;
+  cudaStream_t s = lib_stream();
+  DevInst& I = h->h;
+  I.P = to_dev(p);
+  I.N = N;
+  I.evcap = (int)N;
+  std::vector<Tile> tl = make_tiles(0, p->nx, p->ny);
+  I.ntiles = (int)tl.size();
+  h->ntiles = I.ntiles;
+  pslbm_status st = PSLBM_OK;
+  void* ptr;
+#define AL(field, bytes)                                     \
+  do {                                                       \
+    st = dalloc(h, &ptr, (bytes));                           \
+    if (st != PSLBM_OK) goto fail_cleanup;                   \
+    field = decltype(field)(ptr);                            \
+  } while (0)
+  for (int b = 0; b < 2; ++b) {
+    AL(I.f[b], (size_t)N * 18 * fsize(p->precision));
+    AL(I.g[b], (size_t)N * 5 * ns * gsize(p->precision));
+    AL(I.type[b], (size_t)N);
+  }
+  AL(I.V, (size_t)N * 2 * sizeof(double));
+  AL(I.q, (size_t)N * 8 * sizeof(double));
+  AL(I.evt, (size_t)N);
+  AL(I.xs, (size_t)N * sizeof(double));
+  AL(I.evlist, (size_t)N * 2 * sizeof(int));
+  AL(I.claim, (size_t)N * sizeof(int));
+  AL(I.scal, S_NSCAL * sizeof(unsigned long long));
+  AL(h->d, sizeof(DevInst));
+  AL(h->tiles, tl.size() * sizeof(Tile));
+  {
+    // staging copies of the inputs
+    uint8_t* dmask = nullptr;
+    double *dr1 = nullptr, *dr2 = nullptr, *dc = nullptr;
+    void* tmp;
+    std::vector<void*> stage;
+    auto salloc = [&](void** pp, size_t b) {
+      cudaError_t e = cudaMalloc(pp, b ? b : 16);
+      if (e == cudaSuccess) stage.push_back(*pp);
+      return e;
+    };
+    cudaError_t e = salloc(&tmp, N);
+    dmask = (uint8_t*)tmp;
+    if (e == cudaSuccess) e = salloc(&tmp, N * sizeof(double)), dr1 = (double*)tmp;
+    if (e == cudaSuccess) e = salloc(&tmp, N * sizeof(double)), dr2 = (double*)tmp;
+    if (e == cudaSuccess && conc && ns) e = salloc(&tmp, N * ns * sizeof(double)), dc = (double*)tmp;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmask, mask, N, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dr1, rho1, N * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dr2, rho2, N * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && dc) e = cudaMemcpyAsync(dc, conc, N * ns * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.q, 0, (size_t)N * 8 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.evt, 0, (size_t)N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.claim, 0, (size_t)N * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.scal, 0, S_NSCAL * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.f[1], 0, (size_t)N * 18 * fsize(p->precision), s);
+    if (e == cudaSuccess && ns) e = cudaMemsetAsync(I.g[1], 0, (size_t)N * 5 * ns * gsize(p->precision), s);
+    if (e == cudaSuccess) {
+      if (vol) {
+        e = cudaMemcpyAsync(I.V, vol, (size_t)N * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+      } else {
+        std::vector<double> v0((size_t)N * 2, 0.0);
+        for (long long i = 0; i < N; ++i) {
+          v0[i] = (mask[i] & 15) == PSLBM_SOLID_D ? 1.0 : 0.0;
+          v0[N + i] = (mask[i] & 15) == PSLBM_SOLID_F ? 1.0 : 0.0;
+        }
+        e = cudaMemcpyAsync(I.V, v0.data(), (size_t)N * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d, &I, sizeof(DevInst), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      L->init(s, h->d, dmask, dr1, dr2, dc, N);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (void* q : stage) cudaFree(q);
+    if (e != cudaSuccess) {
+      st = fail(nullptr, e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA,
+                std::string("create: ") + cudaGetErrorString(e));
+      goto fail_cleanup;
+    }
+  }
+  {
+    // initial liquid threshold: half the maximum initial rho_1 over fluid nodes
+    double* part = nullptr;
+    double* res = nullptr;
+    cudaError_t e = cudaMalloc(&part, BUD_BLOCKS * NBUD * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&res, NBUD * sizeof(double));
+    if (e == cudaSuccess) {
+      L->budget(s, h->d, part, res);
+      e = cudaGetLastError();
+    }
+    double b[NBUD];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b, res, sizeof b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (part) cudaFree(part);
+    if (res) cudaFree(res);
+    if (e == cudaSuccess) {
+      unsigned long long enc = 0;
+      if (b[0] > -INFINITY) {
+        unsigned long long bits;
+        std::memcpy(&bits, &b[0], 8);
+        enc = (bits & 0x8000000000000000ULL) ? ~bits : (bits | 0x8000000000000000ULL);
+      }
+      e = cudaMemcpyAsync(I.scal + S_MAX0, &enc, sizeof enc, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+      st = fail(nullptr, PSLBM_ERR_CUDA, std::string("create threshold: ") + cudaGetErrorString(e));
+      goto fail_cleanup;
+    }
+  }
+#undef AL
+  *out = h;
+  return PSLBM_OK;
+fail_cleanup : {
+  std::string m = h->err;
+  free_all(h);
+  delete h;
+  if (!m.empty()) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_lib_err = m;
+  }
+  return st;
+}
+}
+
+pslbm_status pslbm_step(pslbm_t h, int64_t n) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (h->sticky) return h->sticky;
+  if (n < 0) return fail(h, PSLBM_ERR_PARAM, "n < 0");
+  if (h->in_batch) return fail(h, PSLBM_ERR_STATE, "handle is a member of a batch; step the batch");
+  if (n == 0) return PSLBM_OK;
+  std::string err;
+  pslbm_status st = run_steps(h->graphs, h->L, h->tiles, h->ntiles, h->d, 1, n, err);
+  if (st != PSLBM_OK) return fail(h, st, err);
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_sync(pslbm_t h) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (h->sticky) return h->sticky;
+  cudaError_t e = cudaStreamSynchronize(lib_stream());
+  if (e != cudaSuccess) return fail(h, PSLBM_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+  return device_status(h);
+}
+
+pslbm_status pslbm_info(pslbm_t h, int64_t* steps, int32_t* nx, int32_t* ny, int32_t* n_species) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (steps) {
+    unsigned long long t = 0;
+    CK(h, cudaMemcpyAsync(&t, h->h.scal + S_STEP, sizeof t, cudaMemcpyDeviceToHost, lib_stream()));
+    CK(h, cudaStreamSynchronize(lib_stream()));
+    *steps = (int64_t)t;
+  }
+  if (nx) *nx = h->p.nx;
+  if (ny) *ny = h->p.ny;
+  if (n_species) *n_species = h->ns;
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_device_bytes(pslbm_t h, uint64_t* bytes) {
+  if (!h || !bytes) return fail(h, PSLBM_ERR_PARAM, "NULL argument");
+  *bytes = h->bytes;
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_read_fields(pslbm_t h, uint32_t fields, void* const* out) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (h->sticky) return h->sticky;
+  if (fields & ~0xFFu) return fail(h, PSLBM_ERR_PARAM, "unknown field bits");
+  if (fields && !out) return fail(h, PSLBM_ERR_PARAM, "out is NULL");
+  const long long N = h->N;
+  const int ns = h->ns;
+  cudaStream_t s = lib_stream();
+  // scratch: rho1, rho2, ux, uy (N each), conc (ns N), type (N bytes), budget partials
+  const size_t need = (size_t)N * (4 + ns) * sizeof(double) + (size_t)N + (BUD_BLOCKS + 1) * NBUD * sizeof(double) + 64;
+  if (h->rb_bytes < need) {
+    if (h->rb) {
+      cudaFree(h->rb);
+      h->bytes -= h->rb_bytes;
+    }
+    h->rb = nullptr;
+    h->rb_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->rb, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, PSLBM_ERR_OOM, "read-back scratch allocation failed");
+    }
+    h->rb_bytes = need;
+    h->bytes += need;
+  }
+  double* r1 = h->rb;
+  double* r2 = r1 + N;
+  double* ux = r2 + N;
+  double* uy = ux + N;
+  double* cc = uy + N;
+  double* part = cc + (size_t)N * ns;
+  double* bud = part + BUD_BLOCKS * NBUD;
+  uint8_t* ty = (uint8_t*)(bud + NBUD);
+  h->L->fields(s, h->d, N, r1, r2, ux, uy, ns ? cc : nullptr, ty);
+  CK(h, cudaGetLastError());
+  if (fields & PSLBM_F_BUDGET) {
+    h->L->budget(s, h->d, part, bud);
+    CK(h, cudaGetLastError());
+  }
+  int i = 0;
+  auto cp = [&](void* dst, const void* src, size_t b) {
+    return cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, s);
+  };
+  if (fields & PSLBM_F_RHO1) CK(h, cp(out[i++], r1, N * 8));
+  if (fields & PSLBM_F_RHO2) CK(h, cp(out[i++], r2, N * 8));
+  if (fields & PSLBM_F_UX) CK(h, cp(out[i++], ux, N * 8));
+  if (fields & PSLBM_F_UY) CK(h, cp(out[i++], uy, N * 8));
+  if (fields & PSLBM_F_CONC) {
+    if (ns) CK(h, cp(out[i], cc, (size_t)N * ns * 8));
+    ++i;
+  }
+  if (fields & PSLBM_F_TYPE) CK(h, cp(out[i++], ty, N));
+  if (fields & PSLBM_F_VOL) CK(h, cp(out[i++], h->h.V, (size_t)N * 2 * 8));
+  double budget_host[NBUD];
+  unsigned long long stepc = 0;
+  if (fields & PSLBM_F_BUDGET) {
+    CK(h, cp(budget_host, bud, sizeof budget_host));
+    CK(h, cp(&stepc, h->h.scal + S_STEP, sizeof stepc));
+  }
+  CK(h, cudaStreamSynchronize(s));
+  if (fields & PSLBM_F_BUDGET) {
+    double* o = (double*)out[i++];
+    o[0] = budget_host[0] > -INFINITY ? budget_host[0] : 0.0;
+    o[1] = budget_host[1];
+    o[2] = budget_host[2];
+    for (int k = 0; k < ns; ++k) o[3 + k] = budget_host[3 + k];
+    o[3 + ns] = budget_host[3 + MAXS];
+    o[4 + ns] = budget_host[4 + MAXS];
+    o[5 + ns] = (double)stepc;
+  }
+  return device_status(h);
+}
+
+pslbm_status pslbm_destroy(pslbm_t h) {
+  if (!h) return PSLBM_OK;
+  cudaStreamSynchronize(lib_stream());
+  if (h->rb) cudaFree(h->rb);
+  free_all(h);
+  delete h;
+  return PSLBM_OK;
+}
+
+const char* pslbm_last_error(pslbm_t h) {
+  if (h) return h->err.c_str();
+  return g_lib_err.c_str();
+}
+
+// ------------------------------------------------------------------ batches
+
+pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_x, int32_t tile_y,
+                                pslbm_batch_t* out) {
+  if (!out) return fail(nullptr, PSLBM_ERR_PARAM, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !members) return fail(nullptr, PSLBM_ERR_PARAM, "empty batch");
+  if (!((tile_x == 0 || tile_x == TX) && (tile_y == 0 || tile_y == TY)))
+    return fail(nullptr, PSLBM_ERR_PARAM, "unsupported tile shape");
+  for (int i = 0; i < n; ++i) {
+    if (!members[i] || members[i]->sticky) return fail(nullptr, PSLBM_ERR_PARAM, "invalid member");
+    if (members[i]->in_batch) return fail(nullptr, PSLBM_ERR_STATE, "member already in a batch");
+    if (members[i]->prec != members[0]->prec || members[i]->ns != members[0]->ns)
+      return fail(nullptr, PSLBM_ERR_PARAM, "members differ in precision or species count");
+    for (int j = 0; j < i; ++j)
+      if (members[j] == members[i]) return fail(nullptr, PSLBM_ERR_PARAM, "duplicate member");
+  }
+  pslbm_batch_t b = new (std::nothrow) pslbm_batch_s();
+  if (!b) return fail(nullptr, PSLBM_ERR_OOM, "host allocation failed");
+  std::vector<DevInst> di;
+  std::vector<Tile> tl;
+  for (int i = 0; i < n; ++i) {
+    b->members.push_back(members[i]);
+    di.push_back(members[i]->h);
+    std::vector<Tile> t = make_tiles(i, members[i]->p.nx, members[i]->p.ny);
+    tl.insert(tl.end(), t.begin(), t.end());
+  }
+  cudaStream_t s = lib_stream();
+  cudaError_t e = cudaMalloc(&b->d, di.size() * sizeof(DevInst));
+  if (e == cudaSuccess) e = cudaMalloc(&b->tiles, tl.size() * sizeof(Tile));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d, di.data(), di.size() * sizeof(DevInst), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    if (b->d) cudaFree(b->d);
+    if (b->tiles) cudaFree(b->tiles);
+    delete b;
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA,
+                std::string("batch create: ") + cudaGetErrorString(e));
+  }
+  b->ntiles = (int)tl.size();
+  b->L = members[0]->L;
+  for (int i = 0; i < n; ++i) members[i]->in_batch = 1;
+  *out = b;
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_batch_step(pslbm_batch_t b, int64_t n) {
+  if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
+  if (b->sticky) return b->sticky;
+  if (n < 0) return fail(nullptr, PSLBM_ERR_PARAM, "n < 0");
+  if (n == 0) return PSLBM_OK;
+  std::string err;
+  pslbm_status st = run_steps(b->graphs, b->L, b->tiles, b->ntiles, b->d, (int)b->members.size(), n, err);
+  if (st != PSLBM_OK) {
+    b->sticky = st;
+    b->err = err;
+    return fail(nullptr, st, err);
+  }
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_batch_sync(pslbm_batch_t b) {
+  if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
+  if (b->sticky) return b->sticky;
+  cudaError_t e = cudaStreamSynchronize(lib_stream());
+  if (e != cudaSuccess) return fail(nullptr, PSLBM_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(e));
+  for (pslbm_t m : b->members) {
+    pslbm_status st = device_status(m);
+    if (st != PSLBM_OK) return st;
+  }
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_batch_destroy(pslbm_batch_t b) {
+  if (!b) return PSLBM_OK;
+  cudaStreamSynchronize(lib_stream());
+  b->graphs.clear();
+  if (b->d) cudaFree(b->d);
+  if (b->tiles) cudaFree(b->tiles);
+  for (pslbm_t m : b->members) m->in_batch = 0;
+  delete b;
+  return PSLBM_OK;
+}
+
+}  // extern "C"
+
+namespace pslbm {
+
+const Launchers* launchers_f64(int ns);
+const Launchers* launchers_f32(int ns);
+const Launchers* launchers_f32h(int ns);
+const Launchers* launchers_f32b(int ns);
+
+const Launchers* launchers(int prec, int ns) {
+  switch (prec) {
+    case PSLBM_FP64: return launchers_f64(ns);
+    case PSLBM_FP32: return launchers_f32(ns);
+    case PSLBM_FP32_SOLUTE_F16: return launchers_f32h(ns);
+    case PSLBM_FP32_SOLUTE_BF16: return launchers_f32b(ns);
+  }
+  return nullptr;
+}
+
+}  // namespace pslbm
