@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the reactive two-phase LBM step on GB300.
+
+Workload: the porous-medium reactive two-phase lattice (1024x512, seeded
+overlapping D(s) discs of radius 8-24 at porosity 0.6, inlet reservoir with
+liquid and gas slugs, outlet reservoir, species B, E, F transported and A
+derived, R1-R4), FP32 compute with shifted FP32 storage.  One step is one pass
+of the whole hot path: the fused bulk kernel, the VOP kernel and the
+amendment kernel.
+
+Prints one JSON line (rank 0).  Metric: MLUPS (all lattice nodes x steps / s,
+whole job).  L2 is flushed (256 MiB write) before every timed step; each step
+is timed with CUDA events on the library stream.
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (256x128, same generator) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(nx=1024, ny=512, seed=1)
+SAMPLE = dict(nx=256, ny=128, seed=1)
+WORKLOAD_NAME = ("porous discs 1024x512 (radii 8-24, porosity 0.6, seed 1), inlet liquid/gas slugs + outlet, "
+                 "species B,E,F transported + A derived, R1-R4 (k1=1e-5, k3=1e-1, k2=1e-3, k4=1e-3)")
+PROFILE_JSON = os.path.join(ROOT, "profiles", "k_bulk_porous1024x512_fp32.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_f16", "fp32_bf16"], default="fp32")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline and e2e legs")
+    return ap.parse_args()
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1410_3464_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_run(seconds_budget, max_steps=None, warmup=1):
+    """Time the CPU oracle on the bounded sample; returns (MLUPS, steps, seconds)."""
+    from oracle import lbm
+    from paper_1410_3464_gb300 import inputs
+    sc = inputs.porous_discs(**SAMPLE)
+    L = lbm.Lattice(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"])
+    for _ in range(warmup):
+        L.step()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        L.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and n >= max_steps) or (max_steps is None and el >= seconds_budget):
+            break
+    nodes = SAMPLE["nx"] * SAMPLE["ny"]
+    return nodes * n / el / 1e6, n, el
+
+
+def sample_desc(n, el):
+    return (f"CPU oracle (numpy FP64, one thread) on the same generator at {SAMPLE['nx']}x{SAMPLE['ny']} "
+            f"(seed {SAMPLE['seed']}): {n} steps in {el:.1f} s")
+
+
+# ------------------------------------------------------------------ arms
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    mlups_w, _, _ = oracle_run(0, max_steps=max(1, args.warmup), warmup=0)
+    mlups, n, el = oracle_run(0, max_steps=args.steps, warmup=0)
+    line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD_NAME, "sample": f"{SAMPLE['nx']}x{SAMPLE['ny']}"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample_desc(n, el)},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1410_3464_gb300 import inputs, pslbm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("gloo", init_method="env://")
+    torch.cuda.set_device(local)
+    prec = {"fp32": pslbm.FP32, "fp64": pslbm.FP64, "fp32_f16": pslbm.FP32_SOLUTE_F16,
+            "fp32_bf16": pslbm.FP32_SOLUTE_BF16}[args.precision]
+    fs = 8 if prec == pslbm.FP64 else 4
+    gs = {pslbm.FP64: 8, pslbm.FP32: 4}.get(prec, 2)
+    sc = inputs.porous_discs(**WORKLOAD)
+    N = WORKLOAD["nx"] * WORKLOAD["ny"]
+    ns = sc["params"]["n_species"]
+
+    stream = torch.cuda.ExternalStream(pslbm.get_stream())
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    sim = pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"], precision=prec)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            sim.step(1)
+        torch.cuda.synchronize()
+    t = sim.read(pslbm.F_TYPE)["type"]
+    n_fluid = int((t <= 1).sum())
+    n_liq = int((t == 0).sum())
+
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    kern = {"bulk": [], "vop": [], "amend": []}
+    tot = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            k, total = sim.profile_step(1)
+            for key in kern:
+                kern[key].append(k[key])
+            tot.append(total)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sim.sync()
+    my_ms = float(sum(tot))
+    if ws > 1:
+        tt = torch.tensor([my_ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        my_ms = float(tt.item())
+    total_nodes = N * args.steps * ws
+    value = total_nodes / (my_ms * 1e-3) / 1e6
+    bulk_ms = statistics.mean(kern["bulk"])
+    bytes_per_launch = n_fluid * 36 * fs + n_liq * 10 * ns * gs + 2 * N
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_per_launch / (bulk_ms * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(PROFILE_JSON) and prec == pslbm.FP32:
+        pj = json.load(open(PROFILE_JSON))
+        if pj.get("source_hash") == kernel_source_hash():
+            traffic = pj.get("dram_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_bulk", "bytes_per_launch": bytes_per_launch,
+                "kernel_ms": bulk_ms, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "kernel_share": bulk_ms / statistics.mean(tot)}
+
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": my_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "fp32", "fp64": "f64", "fp32_f16": "fp32 (f16 solute storage)",
+                      "fp32_bf16": "fp32 (bf16 solute storage)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "nx": WORKLOAD["nx"], "ny": WORKLOAD["ny"],
+                       "fluid_nodes": n_fluid, "liquid_nodes": n_liq, "precision": args.precision,
+                       "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
+            "roofline": roofline,
+            "kernel_ms": {k: statistics.mean(v) for k, v in kern.items()},
+            "gpu_launches": 3 * args.steps}
+    if clk:
+        line["clocks"] = clk
+
+    if not args.skip_cpu:
+        # end to end through the C ABI with host buffers: create (H2D of the
+        # initial state), K steps, read of all fields (D2H)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2 = pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                                precision=prec)
+        sim2.step(args.steps)
+        out = sim2.read(pslbm.F_RHO1 | pslbm.F_RHO2 | pslbm.F_UX | pslbm.F_UY | pslbm.F_CONC | pslbm.F_TYPE |
+                        pslbm.F_VOL)
+        el = time.perf_counter() - t0
+        sim2.close()
+        h2d = sc["mask"].nbytes + sc["rho1"].nbytes + sc["rho2"].nbytes + sc["conc"].nbytes
+        d2h = sum(v.nbytes for k, v in out.items() if k not in ("vol_d", "vol_f"))
+        e2e_val = N * args.steps / el / 1e6
+        if ws > 1:
+            tt = torch.tensor([el], dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_val = N * args.steps * ws / float(tt.item()) / 1e6
+        line["e2e"] = {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                       "d2h_bytes_per_step": d2h / args.steps,
+                       "note": "initial state copied at create, all fields read back after the last step"}
+        if rank == 0:
+            mlups, n, elc = oracle_run(10.0)
+            line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                    "sample": sample_desc(n, elc)}
+    sim.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

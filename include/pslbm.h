@@ -156,6 +156,14 @@ pslbm_status pslbm_sync(pslbm_t h);
  * (one per selected field, in bit order).  Synchronises the stream. */
 pslbm_status pslbm_read_fields(pslbm_t h, uint32_t fields, void* const* out);
 
+/* Run n >= 1 steps without graph capture, timing each kernel with CUDA
+ * events on the library stream, and synchronise.  kernel_ms[3] receives the
+ * mean duration per step (ms) of the bulk kernel (Eqs. 6-31 fused), the VOP
+ * kernel (Eqs. 32-35) and the amendment kernel (Section 4.5); total_ms the
+ * mean time per step from the first to the last event.  Same results as
+ * pslbm_step. */
+pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double* total_ms);
+
 /* Number of steps taken and lattice size. */
 pslbm_status pslbm_info(pslbm_t h, int64_t* steps, int32_t* nx, int32_t* ny, int32_t* n_species);
 

@@ -462,6 +462,44 @@ pslbm_status pslbm_step(pslbm_t h, int64_t n) {
   return PSLBM_OK;
 }
 
+pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double* total_ms) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (h->sticky) return h->sticky;
+  if (n < 1 || !kernel_ms) return fail(h, PSLBM_ERR_PARAM, "n < 1 or kernel_ms is NULL");
+  if (h->in_batch) return fail(h, PSLBM_ERR_STATE, "handle is a member of a batch");
+  cudaStream_t s = lib_stream();
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) CK(h, cudaEventCreate(&ev[i]));
+  double acc[3] = {0, 0, 0}, tot = 0;
+  pslbm_status st = PSLBM_OK;
+  for (int64_t i = 0; i < n && st == PSLBM_OK; ++i) {
+    cudaEventRecord(ev[0], s);
+    h->L->bulk(s, h->tiles, h->ntiles, h->d);
+    cudaEventRecord(ev[1], s);
+    launch_vop(s, h->tiles, h->ntiles, h->d);
+    cudaEventRecord(ev[2], s);
+    h->L->amend(s, 1, h->d);
+    cudaEventRecord(ev[3], s);
+    cudaError_t e = cudaEventSynchronize(ev[3]);
+    if (e != cudaSuccess) {
+      st = fail(h, PSLBM_ERR_CUDA, std::string("profile step: ") + cudaGetErrorString(e));
+      break;
+    }
+    float ms;
+    for (int k = 0; k < 3; ++k) {
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+    cudaEventElapsedTime(&ms, ev[0], ev[3]);
+    tot += ms;
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (st != PSLBM_OK) return st;
+  for (int k = 0; k < 3; ++k) kernel_ms[k] = acc[k] / double(n);
+  if (total_ms) *total_ms = tot / double(n);
+  return device_status(h);
+}
+
 pslbm_status pslbm_sync(pslbm_t h) {
   if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
   if (h->sticky) return h->sticky;

@@ -23,6 +23,7 @@ STATUS = {0: "OK", -1: "ERR_PARAM", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NONF
           -5: "ERR_EOS_DOMAIN", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_NODEVICE"}
 
 EXPORTS = ["pslbm_get_stream", "pslbm_set_stream", "pslbm_create", "pslbm_step", "pslbm_sync",
+           "pslbm_profile_step",
            "pslbm_read_fields", "pslbm_info", "pslbm_device_bytes", "pslbm_destroy", "pslbm_last_error",
            "pslbm_batch_create", "pslbm_batch_step", "pslbm_batch_sync", "pslbm_batch_destroy"]
 
@@ -96,6 +97,7 @@ def load():
     lib.pslbm_create.argtypes = [vp, vp, vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
     lib.pslbm_step.argtypes = [vp, i64]
     lib.pslbm_sync.argtypes = [vp]
+    lib.pslbm_profile_step.argtypes = [vp, i64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.pslbm_read_fields.argtypes = [vp, u32, C.POINTER(vp)]
     lib.pslbm_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.pslbm_device_bytes.argtypes = [vp, C.POINTER(C.c_uint64)]
@@ -160,6 +162,14 @@ class Simulation:
 
     def sync(self):
         _check(load().pslbm_sync(self.h), self.h)
+
+    def profile_step(self, n=1):
+        """Run n steps with per-kernel CUDA-event timing; returns
+        ({'bulk', 'vop', 'amend'} mean ms per step, mean total ms per step)."""
+        k = (C.c_double * 3)()
+        t = C.c_double()
+        _check(load().pslbm_profile_step(self.h, int(n), k, C.byref(t)), self.h)
+        return dict(bulk=k[0], vop=k[1], amend=k[2]), t.value
 
     def steps(self):
         t = C.c_int64()

@@ -205,7 +205,7 @@ def test_porous_full_size_1024x512(pslbm):
 def test_batch_equals_alone(pslbm):
     """Two simulations of different sizes stepped as one batch give bit-identical
     fields to the same simulations stepped alone."""
-    a = inputs.bubble_grain(nx=64, ny=32, grain=(40, 16, 6), bubble=(14, 16, 5))
+    a = inputs.porous_discs(nx=72, ny=48, seed=5, slug=(8, 4))
     b = inputs.porous_discs(nx=96, ny=40, seed=3, slug=(10, 5))
     alone = []
     for sc in (a, b):
