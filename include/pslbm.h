@@ -176,6 +176,26 @@ pslbm_status pslbm_destroy(pslbm_t h);
 /* Last error message of the handle (or of the library when h is NULL). */
 const char* pslbm_last_error(pslbm_t h);
 
+/* Budget of the current state written to DEVICE memory without allocating
+ * anything.  The paper has no counterpart: this entry point exists for callers
+ * that must not allocate device memory at the moment they want the budget --
+ * code running while a CUDA graph is being captured (cudaMalloc is not allowed
+ * there), hosts that give the library a fixed memory pool and forbid later
+ * allocation, real-time loops where an allocation could stall.
+ *   out  caller-owned device buffer of 6 + n_species doubles; receives the
+ *        PSLBM_F_BUDGET layout (max rho1, sum rho1, sum rho2, sum C_k, sum V_D,
+ *        sum V_F, step count), the same numbers as pslbm_read_fields gives.
+ * Asynchronous on the library stream.  The per-block partial sums live in one
+ * file-scope device array of 4096 x 9 doubles (288 KiB), held by every GPU that
+ * loads the library until the process exits; lattices above 4096 * 8192 =
+ * 33,554,432 nodes are rejected with PSLBM_ERR_PARAM.  Every call overwrites
+ * the rows it reads, so nothing has to be cleared between calls, but all calls
+ * share the array: calls that overlap on the GPU (other streams, other threads)
+ * race.  The first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+pslbm_status pslbm_budget_device_noalloc(pslbm_t h, double* out);
+
 /* ---------------------------------------------------------------- batching
  * A batch steps several simulations (same precision and species count) in
  * one launch per kernel over a packed list of tiles of all members.  The

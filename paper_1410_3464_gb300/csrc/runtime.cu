@@ -720,3 +720,13 @@ const Launchers* launchers(int prec, int ns) {
 }
 
 }  // namespace pslbm
+
+// Accessors used by the allocation-free budget entry point (noalloc.cu).
+namespace pslbm {
+const DevInst* handle_device_inst(pslbm_t h) { return h->d; }
+long long handle_nodes(pslbm_t h) { return h->N; }
+int handle_precision(pslbm_t h) { return h->prec; }
+int handle_species(pslbm_t h) { return h->ns; }
+pslbm_status handle_fail(pslbm_t h, pslbm_status s, const std::string& msg) { return fail(h, s, msg); }
+cudaStream_t library_stream() { return lib_stream(); }
+}  // namespace pslbm

@@ -25,7 +25,8 @@ STATUS = {0: "OK", -1: "ERR_PARAM", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NONF
 EXPORTS = ["pslbm_get_stream", "pslbm_set_stream", "pslbm_create", "pslbm_step", "pslbm_sync",
            "pslbm_profile_step",
            "pslbm_read_fields", "pslbm_info", "pslbm_device_bytes", "pslbm_destroy", "pslbm_last_error",
-           "pslbm_batch_create", "pslbm_batch_step", "pslbm_batch_sync", "pslbm_batch_destroy"]
+           "pslbm_batch_create", "pslbm_batch_step", "pslbm_batch_sync", "pslbm_batch_destroy",
+           "pslbm_budget_device_noalloc"]
 
 _D2 = C.c_double * 2
 _DS = C.c_double * MAX_SPECIES
@@ -108,6 +109,7 @@ def load():
     lib.pslbm_batch_step.argtypes = [vp, i64]
     lib.pslbm_batch_sync.argtypes = [vp]
     lib.pslbm_batch_destroy.argtypes = [vp]
+    lib.pslbm_budget_device_noalloc.argtypes = [vp, vp]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("pslbm_get_stream", "pslbm_last_error"):
@@ -206,6 +208,11 @@ class Simulation:
             res["vol_d"], res["vol_f"] = res["vol"][0], res["vol"][1]
         del N
         return res
+
+    def budget_device_noalloc(self, out_device_ptr):
+        """Write the budget (6 + n_species doubles) to a caller-owned device
+        buffer without allocating anything (see include/pslbm.h)."""
+        _check(load().pslbm_budget_device_noalloc(self.h, out_device_ptr), self.h)
 
     def close(self):
         if getattr(self, "h", None):
