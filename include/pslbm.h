@@ -74,7 +74,7 @@ enum {
 /* Parameter block.  struct_size must be sizeof(pslbm_params). */
 typedef struct {
     uint32_t struct_size;
-    int32_t nx, ny;                /* lattice size, nx, ny >= 1, nx*ny < 2^31 */
+    int32_t nx, ny;                /* lattice size, nx, ny >= 1, nx*ny <= 100,000,000 */
     int32_t periodic_x, periodic_y;/* 1: periodic axis; 0: outside the edge acts as a wall */
     int32_t precision;             /* pslbm_precision */
     /* fluid: Eqs. 6-19 */
@@ -104,8 +104,11 @@ typedef struct {
     uint64_t seed;                 /* seed of the overflow-neighbour choice (SplitMix64) */
     /* reservoir nodes */
     double rho_in_liq[2], rho_in_gas[2]; /* inlet densities during liquid / gas slugs */
-    double rho_out[2];             /* outlet densities */
+    double rho_out[2];             /* outlet densities while the node upstream (x - 1) is liquid */
+    double rho_out_gas[2];         /* outlet densities while the node upstream is gas */
     int32_t inlet_period_liq, inlet_period_gas; /* slug lengths in steps (gas 0: always liquid) */
+    int32_t inlet_ramp;            /* steps of linear blend between the liquid and gas inlet
+                                      states at the end of each slug (0: sharp switch) */
     double conc_in[PSLBM_MAX_SPECIES];  /* inlet concentrations */
 } pslbm_params;
 

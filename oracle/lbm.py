@@ -152,8 +152,8 @@ def default_params(nx, ny):
         k1=0.0, inv_Keq=0.0, k3=0.0, k2=0.0, k4=0.0, C_F_sat=0.0,
         gas_yield=0.0, inv_M_C=0.0, c_total_per_rho1=0.0,
         Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=0,
-        rho_in_liq=(0.0, 0.0), rho_in_gas=(0.0, 0.0), rho_out=(0.0, 0.0),
-        inlet_period_liq=1, inlet_period_gas=0, conc_in=(0.0,) * MAX_SPECIES,
+        rho_in_liq=(0.0, 0.0), rho_in_gas=(0.0, 0.0), rho_out=(0.0, 0.0), rho_out_gas=(0.0, 0.0),
+        inlet_period_liq=1, inlet_period_gas=0, inlet_ramp=0, conc_in=(0.0,) * MAX_SPECIES,
     )
 
 
@@ -272,7 +272,7 @@ class Lattice:
             c = c + g[a]
         return c
 
-    def _reservoir_state(self, typ, rho1, rho2, jx, jy, t):
+    def _reservoir_state(self, typ, rho1, rho2, jx, jy, t, theta):
         """Reservoir nodes hold a fixed equilibrium state that they push into
         their fluid neighbours: an inlet whose densities alternate between a
         liquid and a gas state (gas slugs), and an outlet at fixed density.  The
@@ -281,11 +281,21 @@ class Lattice:
         p = self.p
         inlet, outlet = typ == INLET, typ == OUTLET
         pl, pg = int(p["inlet_period_liq"]), int(p["inlet_period_gas"])
-        in_liquid = pg <= 0 or (t % (pl + pg)) < pl
-        rin = p["rho_in_liq"] if in_liquid else p["rho_in_gas"]
-        r1 = np.where(inlet, rin[0], np.where(outlet, p["rho_out"][0], 0.0))
-        r2 = np.where(inlet, rin[1], np.where(outlet, p["rho_out"][1], 0.0))
+        ramp = int(p.get("inlet_ramp", 0))
+        wg = 0.0                    # weight of the gas state: slugs with linear ramps
+        if pg > 0:
+            ph = t % (pl + pg)
+            if ph < pl:
+                wg = (ph - (pl - ramp) + 1) / (ramp + 1) if (ramp > 0 and ph >= pl - ramp) else 0.0
+            else:
+                wg = 1.0 - (ph - (pl + pg - ramp) + 1) / (ramp + 1) if (ramp > 0 and ph >= pl + pg - ramp) else 1.0
+        rin = [(1.0 - wg) * p["rho_in_liq"][s] + wg * p["rho_in_gas"][s] for s in range(2)]
         fluid = self._fluid(typ)
+        # outlet: liquid or gas state by the marking of the node upstream (x - 1)
+        up_liq = self.nb(fluid & (rho1 > theta), -1, 0, False)
+        ro = [np.where(up_liq, p["rho_out"][s], p["rho_out_gas"][s]) for s in range(2)]
+        r1 = np.where(inlet, rin[0], np.where(outlet, ro[0], 0.0))
+        r2 = np.where(inlet, rin[1], np.where(outlet, ro[1], 0.0))
         rho = rho1 + rho2
         with np.errstate(invalid="ignore", divide="ignore"):
             ux = np.where(fluid, (jx) / np.where(fluid, rho, 1.0), 0.0)
@@ -390,7 +400,7 @@ class Lattice:
         typ = self.type
         fluid = self._fluid(typ)
         rho1, rho2, j1, j2 = self.moments()
-        r1res, r2res, _, _ = self._reservoir_state(typ, rho1, rho2, j1[0] + j2[0], j1[1] + j2[1], self.t)
+        r1res, r2res, _, _ = self._reservoir_state(typ, rho1, rho2, j1[0] + j2[0], j1[1] + j2[1], self.t, self.theta)
         F = self._forces(typ, rho1, rho2, r1res, r2res)
         with np.errstate(invalid="ignore", divide="ignore"):
             _, _, ur = self._velocities(np.where(fluid, rho1, 1.0), np.where(fluid, rho2, 1.0), j1, j2, F)
@@ -451,7 +461,7 @@ class Lattice:
             raise NonFiniteError("non-finite density")
         theta = self.theta
         new_max = self._fluid_max(rho1, fluid)
-        r1res, r2res, uxres, uyres = self._reservoir_state(typ, rho1, rho2, j1[0] + j2[0], j1[1] + j2[1], t)
+        r1res, r2res, uxres, uyres = self._reservoir_state(typ, rho1, rho2, j1[0] + j2[0], j1[1] + j2[1], t, theta)
         # marking (Section 4.5): liquid iff rho_1 > theta
         liq_new = fluid & (rho1 > theta)
         res_liq = res & (r1res > theta)

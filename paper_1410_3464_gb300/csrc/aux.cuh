@@ -91,7 +91,8 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
             a2 = R(P.shift_f[1]) + density_shifted<R>(F + 9 * N, N, nn);
           } else {
             double u, v;
-            reservoir_rho(P, tn, step, u, v);
+            const R theta = R(0.5 * ord_dec(Ip->scal[S_MAX0 + cur]));
+            reservoir_rho(P, tn, step, tn == T_OUTLET && outlet_up_liquid<R, TF>(P, T, F, (int)N, (int)nn, theta), u, v);
             a1 = R(u);
             a2 = R(v);
           }

@@ -31,7 +31,6 @@ enum {
   S_MAX1 = 2,      // slot for odd steps
   S_STATUS = 3,    // error bits
   S_NEVENT = 4,    // events recorded by the VOP kernel this step
-  S_DONE = 5,      // tiles of the VOP kernel finished this step
   S_NSCAL = 8
 };
 enum { ST_NONFINITE = 1, ST_EOS = 2, ST_EVOVERFLOW = 4 };
@@ -47,17 +46,19 @@ enum { EV_NONE = 0, EV_DISSOLVE = 1, EV_OVERFLOW = 2 };   // overflow: code | (d
 struct DevParams {
   int nx, ny, px, py, ns;
   int iA, iB, iE, iF;
-  int per_liq, per_gas;
+  int per_liq, per_gas, ramp;
   double tau[2], G11, G12, G21, a0, rho10, rho20, w_adh[2];
   double eos_a, eos_b, eos_R, eos_T;
   double gx, gy;
   double shift_f[2];       // population shift rho_ref (0 in FP64 storage)
   double rho_fill[2];      // density of a refilled node without fluid neighbours
   double J0[MAXS], tau_g[MAXS], shift_c[MAXS];
+  double inv_tau[2], Ja[MAXS], inv_tau_g[MAXS];  // 1/tau, (1 - J0)/4, 1/tau_g
+  double cR1[MAXS], cR3[MAXS];                     // S_k = cR1[k] R1 + cR3[k] R3 (Eq. 28)
   double k1, inv_Keq, k3, k2, k4, C_F_sat, gas_yield, inv_M_C, c_total_per_rho1;
   double Vbar_D, Vbar_F, V_split;
   unsigned long long seed;
-  double rho_in_liq[2], rho_in_gas[2], rho_out[2];
+  double rho_in_liq[2], rho_in_gas[2], rho_out[2], rho_out_gas[2];
   double conc_in[MAXS];
 };
 
@@ -67,7 +68,6 @@ struct DevInst {
   void* g[2];                 // [ns][5][N] solute populations, ping-pong
   uint8_t* type[2];           // [N] node types, ping-pong
   double* V;                  // [2][N] V_D, V_F
-  double* q;                  // [2][4][N] link fluxes of B and F toward a mineral (direction 1..4)
   uint8_t* evt;               // [N] VOP events (zero except during a step)
   double* xs;                 // [N] overflow excess of an event node
   int* evlist;                // [evcap] event node indices
@@ -177,17 +177,51 @@ __device__ __forceinline__ R density_c(const TF* f, long long N, long long node)
   return s;
 }
 
-// Reservoir densities at step t (inlet slugs alternate liquid and gas).
-__device__ __forceinline__ void reservoir_rho(const DevParams& P, uint8_t t, unsigned long long step, double& r1,
-                                              double& r2) {
+// Reservoir densities at step t.  The inlet alternates liquid slugs of
+// per_liq steps and gas slugs of per_gas steps; the last `ramp` steps of each
+// slug blend linearly into the next state.  The outlet holds the liquid or the
+// gas state according to the marking of the node upstream of it (x - 1).
+__device__ __forceinline__ void reservoir_rho(const DevParams& P, uint8_t t, unsigned long long step, bool up_liquid,
+                                              double& r1, double& r2) {
   if (t == T_INLET) {
-    bool liq = P.per_gas <= 0 || (long long)(step % (unsigned long long)(P.per_liq + P.per_gas)) < P.per_liq;
-    r1 = liq ? P.rho_in_liq[0] : P.rho_in_gas[0];
-    r2 = liq ? P.rho_in_liq[1] : P.rho_in_gas[1];
+    double wg = 0.0;   // weight of the gas state
+    if (P.per_gas > 0) {
+      const long long per = P.per_liq + P.per_gas;
+      const long long ph = (long long)(step % (unsigned long long)per);
+      const long long R = P.ramp;
+      if (ph < P.per_liq) {
+        wg = (R > 0 && ph >= P.per_liq - R) ? double(ph - (P.per_liq - R) + 1) / double(R + 1) : 0.0;
+      } else {
+        wg = (R > 0 && ph >= per - R) ? 1.0 - double(ph - (per - R) + 1) / double(R + 1) : 1.0;
+      }
+    }
+    r1 = (1.0 - wg) * P.rho_in_liq[0] + wg * P.rho_in_gas[0];
+    r2 = (1.0 - wg) * P.rho_in_liq[1] + wg * P.rho_in_gas[1];
   } else {
-    r1 = P.rho_out[0];
-    r2 = P.rho_out[1];
+    // outlet: the coexistence state of the phase arriving from upstream
+    r1 = up_liquid ? P.rho_out[0] : P.rho_out_gas[0];
+    r2 = up_liquid ? P.rho_out[1] : P.rho_out_gas[1];
   }
+}
+
+// Marking of an arbitrary node from global memory (same arithmetic as the
+// shared-memory path, so both give the same answer bit for bit).
+template <class R, class TF>
+__device__ __forceinline__ bool liquid_at(const DevParams& P, const uint8_t* tin, const TF* fin, int N, int node,
+                                          R theta) {
+  uint8_t t = tin[node] & T_MASK;
+  if (!is_fluid(t)) return false;
+  R rho1 = R(P.shift_f[0]) + density_shifted<R>(fin, (long long)N, node);
+  return rho1 > theta;
+}
+
+// Marking of the node upstream (x - 1) of an outlet node at index idx.
+template <class R, class TF>
+__device__ __forceinline__ bool outlet_up_liquid(const DevParams& P, const uint8_t* tin, const TF* fin, int N, int idx,
+                                                 R theta) {
+  int xn, yn;
+  if (!nbr(P, idx % P.nx, idx / P.nx, -1, 0, xn, yn)) return false;
+  return liquid_at<R, TF>(P, tin, fin, N, yn * P.nx + xn, theta);
 }
 
 // Eq. 12 (C-S EOS) and the Eq. 13 square-root argument.
@@ -199,6 +233,12 @@ template <class R> __device__ __forceinline__ R psi_arg(const DevParams& P, R rh
   return R(6) / R(P.G11) * (p - rho / R(3));
 }
 
+template <class R> __device__ __forceinline__ R rrcp(R v);
+template <> __device__ __forceinline__ double rrcp<double>(double v) { return 1.0 / v; }
+template <> __device__ __forceinline__ float rrcp<float>(float v) { return __frcp_rn(v); }
+template <class R> __device__ __forceinline__ R rmax(R a, R b);
+template <> __device__ __forceinline__ double rmax<double>(double a, double b) { return fmax(a, b); }
+template <> __device__ __forceinline__ float rmax<float>(float a, float b) { return fmaxf(a, b); }
 template <class R> __device__ __forceinline__ R rexp(R v);
 template <> __device__ __forceinline__ double rexp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float rexp<float>(float v) { return expf(v); }

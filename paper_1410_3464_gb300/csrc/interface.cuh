@@ -1,26 +1,153 @@
-// Amendment kernel of one time step (Chen, Kang et al., arXiv 1410.3464):
-// status changes and the amendment of Step 5 (Section 4.5) at nodes flipped
-// by the volume-of-pixel kernel; one block per instance, idle unless the VOP
-// kernel recorded events.  Every gather runs in the fixed order E, N, W, S, so
-// the result does not depend on thread scheduling.
+// Interface kernels of one time step (Chen, Kang et al., arXiv 1410.3464):
+//   k_vop   -- heterogeneous reactions at liquid-mineral links (Eqs. 29-31)
+//              and the volume-of-pixel update (Eqs. 32-35, Step 4) with the
+//              status decisions (dissolution, precipitation overflow);
+//   k_amend -- status changes and the amendment of Step 5 (Section 4.5) at
+//              flipped nodes, one block per instance; it ends the step.
+// Every gather runs in the fixed order E, N, W, S, so the result does not
+// depend on thread scheduling.
 #pragma once
 #include "device.cuh"
 
 namespace pslbm {
 
+// The bulk kernel bounces every solute population that leaves a liquid node
+// toward a mineral back into the node (halfway bounce-back).  At a reactive
+// link this kernel replaces the bounced value by the reactive link rule: with
+// the outgoing population `out`, J_w = (1 - J0)/4 and kappa = k / (2 J_w),
+// the returning population is (out (1 - kappa) + k C_sat) / (1 + kappa) and the
+// link flux q = out - back is the amount consumed (B by R2 at D(s), F by R4 at
+// D(s) or F(s)); E gains the B consumed on the same link.  Then V_D -= Vbar_D
+// sum q_B, V_F += Vbar_F sum q_F, and the node dissolves, overflows or changes
+// between D(s) and F(s).
+template <class TF, class TG, class R, int NS>
+__global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles, int ntiles,
+                                                   const DevInst* __restrict__ insts) {
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const Tile tl = tiles[ti];
+    const DevInst* Ip = insts + tl.inst;
+    const DevParams& P = Ip->P;
+    const int x = tl.x0 + tx, y = tl.y0 + ty;
+    if (x >= P.nx || y >= P.ny) continue;
+    const int N = (int)Ip->N;
+    const unsigned long long step = Ip->scal[S_STEP];
+    const int cur = int(step & 1ULL);
+    uint8_t* tnew = Ip->type[cur ^ 1];
+    const int node = y * P.nx + x;
+    const uint8_t t = tnew[node] & T_MASK;
+    if (!is_mineral(t)) continue;
+    int nbx[4];
+    int nl = 0;
+    int dirs[4];
+#pragma unroll
+    for (int b = 1; b < 5; ++b) {
+      int xn, yn;
+      nbx[b - 1] = -1;
+      if (!nbr(P, x, y, EX(b), EY(b), xn, yn)) continue;
+      const int nn = yn * P.nx + xn;
+      if ((tnew[nn] & T_MASK) != T_LIQUID) continue;
+      nbx[b - 1] = nn;
+      dirs[nl++] = b;
+    }
+    if (nl == 0) continue;
+    double sB = 0.0, sF = 0.0;
+    if constexpr (NS > 0) {
+      TG* gout = (TG*)Ip->g[cur ^ 1];
+      const bool useB = (t == T_SOLID_D) && P.iB >= 0 && P.k2 != 0.0;
+      const bool useF = P.iF >= 0 && P.k4 != 0.0;
+#pragma unroll
+      for (int b = 1; b < 5; ++b) {
+        const int nn = nbx[b - 1];
+        if (nn < 0) continue;
+        // the population that left nn toward this node was bounced into slot b of nn
+        if (useB) {
+          const int iB = P.iB;
+          const R Ja = R(P.Ja[iB]), sh = Ja * R(P.shift_c[iB]);
+          TG* slot = gout + (iB * 5 + b) * N + nn;
+          const R out = ldc<R>(slot) + sh;
+          const R kap = R(P.k2) / (R(2) * Ja);
+          const R bk = out * (R(1) - kap) / (R(1) + kap);
+          const R q = out - bk;
+          st<TG, R>(slot, bk - sh);
+          sB += double(q);
+          if (P.iE >= 0) {
+            TG* se = gout + (P.iE * 5 + b) * N + nn;
+            st<TG, R>(se, ldc<R>(se) + q);
+          }
+        }
+        if (useF) {
+          const int iF = P.iF;
+          const R Ja = R(P.Ja[iF]), sh = Ja * R(P.shift_c[iF]);
+          TG* slot = gout + (iF * 5 + b) * N + nn;
+          const R out = ldc<R>(slot) + sh;
+          const R kap = R(P.k4) / (R(2) * Ja);
+          const R bk = (out * (R(1) - kap) + R(P.k4) * R(P.C_F_sat)) / (R(1) + kap);
+          st<TG, R>(slot, bk - sh);
+          sF += double(out - bk);
+        }
+      }
+    }
+    double VD = Ip->V[node], VF = Ip->V[N + node];
+    if (t == T_SOLID_D) VD = VD - P.Vbar_D * sB;   // Eq. 33
+    VF = VF + P.Vbar_F * sF;                        // Eq. 35 (precipitation adds volume)
+    if (VD < 0.0) VD = 0.0;
+    const double total = VD + VF;
+    int code = EV_NONE;
+    if (total <= 0.0) {
+      VD = 0.0;
+      VF = 0.0;
+      code = EV_DISSOLVE;
+    } else {
+      tnew[node] = VD > 0.0 ? T_SOLID_D : T_SOLID_F;
+      if (total >= P.V_split) {
+        const double excess = total - 1.0;
+        VF = VF - excess;
+        const unsigned long long key = P.seed ^ (step << 40) ^ (unsigned long long)node;
+        const int pick = int(splitmix64(key) % (unsigned long long)nl);
+        code = EV_OVERFLOW | (dirs[pick] << 4);
+        Ip->xs[node] = excess;
+      }
+    }
+    Ip->V[node] = VD;
+    Ip->V[N + node] = VF;
+    if (code != EV_NONE) {
+      Ip->evt[node] = (uint8_t)code;
+      const unsigned long long slot = atomicAdd(&Ip->scal[S_NEVENT], 1ULL);
+      if (slot < (unsigned long long)Ip->evcap)
+        Ip->evlist[slot] = node;
+      else
+        atomicOr(&Ip->scal[S_STATUS], (unsigned long long)ST_EVOVERFLOW);
+    }
+  }
+}
+
 __device__ __forceinline__ bool surv_fluid(uint8_t tf) { return (tf & (T_NEW | T_VANISH)) == 0 && is_fluid(tf & T_MASK); }
 __device__ __forceinline__ bool surv_liquid(uint8_t tf) { return tf == T_LIQUID; }
+
+// End of a step for one instance: advance the step counter and free the
+// threshold slot the bulk kernel read (it receives the maximum two steps later).
+__device__ __forceinline__ void finish_step(const DevInst* Ip, unsigned long long step) {
+  Ip->scal[S_MAX0 + int(step & 1ULL)] = 0ULL;
+  Ip->scal[S_NEVENT] = 0ULL;
+  Ip->scal[S_STEP] = step + 1;
+}
 
 template <class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ insts) {
   const DevInst* Ip = insts + blockIdx.x;
+  const unsigned long long step = Ip->scal[S_STEP];
   const unsigned long long nev_raw = Ip->scal[S_NEVENT];
-  if (nev_raw == 0) return;
+  if (nev_raw == 0) {
+    if (threadIdx.x == 0) finish_step(Ip, step);
+    return;
+  }
   const DevParams& P = Ip->P;
   const long long N = Ip->N;
   const int nev = (int)min(nev_raw, (unsigned long long)Ip->evcap);
-  // the VOP kernel has advanced the step counter: buffer cur is the new state
-  const int cur = int(Ip->scal[S_STEP] & 1ULL);
+  // buffer cur is the state the bulk kernel just wrote
+  const int cur = int(step & 1ULL) ^ 1;
   TF* F = (TF*)Ip->f[cur];
   TG* G = (TG*)Ip->g[cur];
   uint8_t* T = Ip->type[cur];
@@ -193,7 +320,7 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
   for (int i = threadIdx.x; i < nv; i += blockDim.x) Ip->claim[vlist[i]] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < nev; i += blockDim.x) Ip->evt[Ip->evlist[i]] = 0;
-  if (threadIdx.x == 0) Ip->scal[S_NEVENT] = 0;
+  if (threadIdx.x == 0) finish_step(Ip, step);
 }
 
 }  // namespace pslbm

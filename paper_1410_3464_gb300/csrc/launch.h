@@ -7,6 +7,7 @@ namespace pslbm {
 
 struct Launchers {
   void (*bulk)(cudaStream_t, const Tile*, int ntiles, const DevInst*);
+  void (*vop)(cudaStream_t, const Tile*, int ntiles, const DevInst*);
   void (*amend)(cudaStream_t, int ninst, const DevInst*);
   void (*init)(cudaStream_t, DevInst*, const uint8_t*, const double*, const double*, const double*, long long N);
   void (*fields)(cudaStream_t, const DevInst*, long long N, double*, double*, double*, double*, double*, uint8_t*);
@@ -15,6 +16,5 @@ struct Launchers {
 
 // prec: 0 FP64, 1 FP32, 2 FP32 + half solutes, 3 FP32 + bfloat16 solutes; ns 0..MAXS
 const Launchers* launchers(int prec, int ns);
-void launch_vop(cudaStream_t, const Tile*, int ntiles, const DevInst*);
 
 }  // namespace pslbm

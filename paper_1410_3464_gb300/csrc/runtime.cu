@@ -111,7 +111,8 @@ std::string validate(const pslbm_params* p) {
     snprintf(buf, sizeof buf, "struct_size %u != %zu", p->struct_size, sizeof(pslbm_params));
     return buf;
   }
-  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny >= (1LL << 31)) return "bad lattice size";
+  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny > 100000000LL)
+    return "lattice size must be 1..100,000,000 nodes";
   if (p->precision < 0 || p->precision > 3) return "bad precision";
   for (int s = 0; s < 2; ++s)
     if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) return "tau must be > 0.5";
@@ -144,6 +145,9 @@ std::string validate(const pslbm_params* p) {
   if (p->inlet_period_liq < 0 || p->inlet_period_gas < 0 ||
       (p->inlet_period_gas > 0 && p->inlet_period_liq + p->inlet_period_gas <= 0))
     return "bad inlet periods";
+  if (p->inlet_ramp < 0 || (p->inlet_period_gas > 0 &&
+                            (p->inlet_ramp > p->inlet_period_liq || p->inlet_ramp > p->inlet_period_gas)))
+    return "inlet_ramp must be in [0, min(inlet periods)]";
   return "";
 }
 
@@ -160,6 +164,7 @@ DevParams to_dev(const pslbm_params* p) {
   P.iF = p->idx_F;
   P.per_liq = p->inlet_period_liq;
   P.per_gas = p->inlet_period_gas;
+  P.ramp = p->inlet_ramp;
   for (int s = 0; s < 2; ++s) {
     P.tau[s] = p->tau[s];
     P.w_adh[s] = p->w_adh[s];
@@ -168,6 +173,7 @@ DevParams to_dev(const pslbm_params* p) {
     P.rho_in_liq[s] = p->rho_in_liq[s];
     P.rho_in_gas[s] = p->rho_in_gas[s];
     P.rho_out[s] = p->rho_out[s];
+    P.rho_out_gas[s] = p->rho_out_gas[s];
   }
   P.G11 = p->G11;
   P.G12 = p->G12;
@@ -186,6 +192,13 @@ DevParams to_dev(const pslbm_params* p) {
     P.tau_g[k] = k < p->n_species ? p->tau_g[k] : 1.0;
     P.shift_c[k] = p->precision == PSLBM_FP64 ? 0.0 : p->conc_ref[k];
     P.conc_in[k] = p->conc_in[k];
+  }
+  for (int s = 0; s < 2; ++s) P.inv_tau[s] = 1.0 / p->tau[s];
+  for (int k = 0; k < MAXS; ++k) {
+    P.Ja[k] = (1.0 - p->J0[k]) / 4.0;
+    P.inv_tau_g[k] = 1.0 / P.tau_g[k];
+    P.cR1[k] = (k == p->idx_A ? -1.0 : 0.0) + (k == p->idx_B ? 1.0 : 0.0);
+    P.cR3[k] = (k == p->idx_B ? -1.0 : 0.0) + (k == p->idx_E ? -1.0 : 0.0) + (k == p->idx_F ? 1.0 : 0.0);
   }
   P.k1 = p->k1;
   P.inv_Keq = p->inv_Keq;
@@ -236,7 +249,7 @@ void enqueue_steps(cudaStream_t s, const Launchers* L, const Tile* tiles, int nt
                    int64_t n) {
   for (int64_t i = 0; i < n; ++i) {
     L->bulk(s, tiles, ntiles, d);
-    launch_vop(s, tiles, ntiles, d);
+    L->vop(s, tiles, ntiles, d);
     L->amend(s, ninst, d);
   }
 }
@@ -344,7 +357,6 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
     AL(I.type[b], (size_t)N);
   }
   AL(I.V, (size_t)N * 2 * sizeof(double));
-  AL(I.q, (size_t)N * 8 * sizeof(double));
   AL(I.evt, (size_t)N);
   AL(I.xs, (size_t)N * sizeof(double));
   AL(I.evlist, (size_t)N * 2 * sizeof(int));
@@ -372,7 +384,6 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
     if (e == cudaSuccess) e = cudaMemcpyAsync(dr1, rho1, N * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dr2, rho2, N * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && dc) e = cudaMemcpyAsync(dc, conc, N * ns * sizeof(double), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(I.q, 0, (size_t)N * 8 * sizeof(double), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.evt, 0, (size_t)N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.claim, 0, (size_t)N * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.scal, 0, S_NSCAL * sizeof(unsigned long long), s);
@@ -476,7 +487,7 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
     cudaEventRecord(ev[0], s);
     h->L->bulk(s, h->tiles, h->ntiles, h->d);
     cudaEventRecord(ev[1], s);
-    launch_vop(s, h->tiles, h->ntiles, h->d);
+    h->L->vop(s, h->tiles, h->ntiles, h->d);
     cudaEventRecord(ev[2], s);
     h->L->amend(s, 1, h->d);
     cudaEventRecord(ev[3], s);

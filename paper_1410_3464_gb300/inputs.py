@@ -16,10 +16,11 @@ D2Q5 transport with rest fraction J_0):
     bubble r=10 at (24,32), species A (1.0) and B (0.0), A->B at k1=1e-3, B
     consumed at the grain surface at k2=1e-3 (first-order dissolution).
   * porous_discs(): seeded overlapping D(s) discs (radii U[8,24], porosity 0.6)
-    in an x-channel with an inlet reservoir column (alternating liquid and gas
-    slugs) and an outlet reservoir column; species B, E, F transported, A
-    derived from the liquid density; R1 (k1=1e-5, gas-producing), R3 (k3=1e-1),
-    R2 on D(s) (k2=1e-3), R4 on D(s)/F(s) (k4=1e-3).
+    in an x-channel between an inlet reservoir column (liquid at 1 % over the
+    coexistence density) and an outlet reservoir column, with seeded gas slugs
+    (bubbles) in the pore space; species B, E, F transported, A derived from the
+    liquid density; R1 (k1=1e-5, gas-producing), R3 (k3=1e-1), R2 on D(s)
+    (k2=1e-3), R4 on D(s)/F(s) (k4=1e-3).
 """
 from __future__ import annotations
 
@@ -58,8 +59,8 @@ def base_params(nx, ny):
         k1=0.0, inv_Keq=0.0, k3=0.0, k2=0.0, k4=0.0, C_F_sat=0.0,
         gas_yield=0.0, inv_M_C=0.0, c_total_per_rho1=0.0,
         Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=0,
-        rho_in_liq=(0.0, 0.0), rho_in_gas=(0.0, 0.0), rho_out=(0.0, 0.0),
-        inlet_period_liq=1, inlet_period_gas=0, conc_in=(0.0,) * MAX_SPECIES,
+        rho_in_liq=(0.0, 0.0), rho_in_gas=(0.0, 0.0), rho_out=(0.0, 0.0), rho_out_gas=(0.0, 0.0),
+        inlet_period_liq=1, inlet_period_gas=0, inlet_ramp=0, conc_in=(0.0,) * MAX_SPECIES,
     )
 
 
@@ -165,27 +166,56 @@ def discs_mask(nx, ny, seed, rmin=8.0, rmax=24.0, porosity=0.6, buffer=16, walls
 
 
 def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
-                 k1=1e-5, k3=1e-1, k2=1e-3, k4=1e-3, rho2_gas=0.02, rho2_liq=4e-4,
-                 slug=(2000, 500)):
-    """Porous-medium scene with inflow of liquid and gas slugs; rescaled C-S
-    EOS at 0.7 T_c; species B, E, F transported and A derived."""
+                 k1=1e-5, k3=1e-1, k2=1e-3, k4=1e-3, rho2_gas=0.002, rho2_liq=2e-5,
+                 bubbles=None, bubble_r=(4.0, 10.0), slug=None, overpressure=1.01):
+    """Porous-medium scene: pressure-driven flow in x through seeded overlapping
+    D(s) discs, with gas slugs in the pore space carried by the flow.
+
+    The inlet reservoir column holds liquid at `overpressure` times the liquid
+    coexistence density, the outlet column holds the coexistence density.  Gas
+    slugs are seeded bubbles (count ~ pore area / 2000 nodes unless given,
+    radii uniform in `bubble_r`) with a smooth tanh density profile of width 2.
+    `slug=(P_l, P_g)` instead makes the inlet alternate liquid and gas states
+    (sharp switch; used only for short runs).  Original C-S EOS at 0.7 T_c;
+    species B, E, F transported and A derived from the liquid density."""
     mask = discs_mask(nx, ny, seed, rmin, rmax, porosity)
     mask[1:ny - 1, 0] = INLET
     mask[1:ny - 1, nx - 1] = OUTLET
-    rl, rg = COEX_RESCALED_07
-    rho1 = np.where(mask == LIQUID, rl, 0.0)
-    rho2 = np.where(mask == LIQUID, rho2_liq, 0.0)
+    rl, rg = COEX_ORIGINAL_07
+    # mass units of Eq. 25b: C_A = 1 in liquid at rho_l, so M_A = rho_l; the gas
+    # C(g) of R1 is light, M_C = 0.1 M_A (Eq. 27: S_2 = -S_1 = 0.5 R1 M_C)
+    m_gas = 0.1 * rl
+    y, x = np.mgrid[0:ny, 0:nx]
+    pore = mask == LIQUID
+    rng = _splitmix64_stream(seed * 7919 + 17)
+    if bubbles is None:
+        bubbles = max(1, int(pore.sum() // 2000))
+    bubbles = int(bubbles)
+    prof = np.zeros((ny, nx))          # 1 inside gas, 0 in liquid
+    for _ in range(bubbles):
+        for _try in range(100):
+            cx = 16 + next(rng) * (nx - 32)
+            cy = next(rng) * ny
+            if pore[int(cy), int(cx)]:
+                break
+        r = bubble_r[0] + next(rng) * (bubble_r[1] - bubble_r[0])
+        d = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+        prof = np.maximum(prof, 0.5 * (1.0 - np.tanh((d - r) / 2.0)))
+    prof = np.where(pore, prof, 0.0)
+    mask[pore & (prof > 0.5)] = GAS
+    fluid = (mask == LIQUID) | (mask == GAS)
+    rho1 = np.where(fluid, rl + (rg - rl) * prof, 0.0)
+    rho2 = np.where(fluid, rho2_liq + (rho2_gas - rho2_liq) * prof, 0.0)
     p = base_params(nx, ny)
-    p.update(periodic_x=0, periodic_y=0,
-             eos_a=CS_RESCALED["eos_a"], eos_b=CS_RESCALED["eos_b"], eos_R=CS_RESCALED["eos_R"],
-             eos_T=0.7 * CS_RESCALED["Tc"], rho_ref=(rl, rho2_liq),
+    p.update(periodic_x=0, periodic_y=0, rho_ref=(rl, rho2_liq),
              n_species=3, idx_A=IDX_DERIVED, idx_B=0, idx_E=1, idx_F=2,
              J0=_pad([1.0 / 3.0] * 3), tau_g=_pad([0.8] * 3, 1.0), conc_ref=_pad([0.0] * 3),
              k1=k1, k3=k3, k2=k2, k4=k4, C_F_sat=0.0,
-             gas_yield=0.5, inv_M_C=1.0, c_total_per_rho1=1.0 / rl,
+             gas_yield=0.5 * m_gas, inv_M_C=1.0 / m_gas, c_total_per_rho1=1.0 / rl,
              Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=seed,
-             rho_in_liq=(1.01 * rl, rho2_liq), rho_in_gas=(rg, rho2_gas),
-             rho_out=(rl, rho2_liq), inlet_period_liq=int(slug[0]), inlet_period_gas=int(slug[1]),
-             conc_in=_pad([0.0] * 3))
+             rho_in_liq=(overpressure * rl, rho2_liq), rho_in_gas=(rg, rho2_gas),
+             rho_out=(rl, rho2_liq), rho_out_gas=(rg, rho2_gas), conc_in=_pad([0.0] * 3))
+    if slug is not None:
+        p.update(inlet_period_liq=int(slug[0]), inlet_period_gas=int(slug[1]))
     conc = np.zeros((3, ny, nx))
     return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)

@@ -48,8 +48,8 @@ class Params(C.Structure):
         ("k2", C.c_double), ("k4", C.c_double), ("C_F_sat", C.c_double),
         ("gas_yield", C.c_double), ("inv_M_C", C.c_double), ("c_total_per_rho1", C.c_double),
         ("Vbar_D", C.c_double), ("Vbar_F", C.c_double), ("V_split", C.c_double), ("seed", C.c_uint64),
-        ("rho_in_liq", _D2), ("rho_in_gas", _D2), ("rho_out", _D2),
-        ("inlet_period_liq", C.c_int32), ("inlet_period_gas", C.c_int32),
+        ("rho_in_liq", _D2), ("rho_in_gas", _D2), ("rho_out", _D2), ("rho_out_gas", _D2),
+        ("inlet_period_liq", C.c_int32), ("inlet_period_gas", C.c_int32), ("inlet_ramp", C.c_int32),
         ("conc_in", _DS),
     ]
 
