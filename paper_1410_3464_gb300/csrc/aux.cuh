@@ -22,17 +22,17 @@ __global__ void k_init(DevInst* __restrict__ Ip, const uint8_t* __restrict__ mas
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const R w = w9<R>(a);
-      st<TF, R>(F + a * N + node, fl ? w * r1 - w * R(P.shift_f[0]) : R(0));
-      st<TF, R>(F + (9 + a) * N + node, fl ? w * r2 - w * R(P.shift_f[1]) : R(0));
+      st<TF, R>(F + a * N + node, fl ? w * r1 - w * rp<R>(P).shift_f[0] : R(0));
+      st<TF, R>(F + (9 + a) * N + node, fl ? w * r2 - w * rp<R>(P).shift_f[1] : R(0));
     }
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       const R c = (t == T_LIQUID && conc) ? R(conc[k * N + node]) : R(0);
-      const R J0 = R(P.J0[k]), Ja = (R(1) - J0) / R(4);
+      const R J0 = rp<R>(P).J0[k], Ja = (R(1) - J0) / R(4);
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
         const R ja = a == 0 ? J0 : Ja;
-        st<TG, R>(G + ((long long)k * 5 + a) * N + node, ja * c - ja * R(P.shift_c[k]));
+        st<TG, R>(G + ((long long)k * 5 + a) * N + node, ja * c - ja * rp<R>(P).shift_c[k]);
       }
     }
   }
@@ -69,7 +69,7 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
       R d1 = f1[0], d2 = f2[0];
 #pragma unroll
       for (int a = 1; a < 9; ++a) { d1 += f1[a]; d2 += f2[a]; }
-      const R rho1 = R(P.shift_f[0]) + d1, rho2 = R(P.shift_f[1]) + d2;
+      const R rho1 = rp<R>(P).shift_f[0] + d1, rho2 = rp<R>(P).shift_f[1] + d2;
       const R j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
       const R j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
       const R j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
@@ -87,8 +87,8 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
         if (is_live(tn)) {
           R a1, a2;
           if (is_fluid(tn)) {
-            a1 = R(P.shift_f[0]) + density_shifted<R>(F, N, nn);
-            a2 = R(P.shift_f[1]) + density_shifted<R>(F + 9 * N, N, nn);
+            a1 = rp<R>(P).shift_f[0] + density_shifted<R>(F, N, nn);
+            a2 = rp<R>(P).shift_f[1] + density_shifted<R>(F + 9 * N, N, nn);
           } else {
             double u, v;
             const R theta = R(0.5 * ord_dec(Ip->scal[S_MAX0 + cur]));
@@ -106,11 +106,11 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
         if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
         if (EY(a) < 0) { spy -= vp; s2y -= v2; s1y -= v1; ssy -= vs; }
       }
-      const R G11 = R(P.G11), G12 = R(P.G12), G21 = R(P.G21), w1 = R(P.w_adh[0]), w2 = R(P.w_adh[1]);
-      const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * R(P.gx);
-      const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * R(P.gy);
-      const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * R(P.gx);
-      const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * R(P.gy);
+      const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0], w2 = rp<R>(P).w_adh[1];
+      const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * rp<R>(P).gx;
+      const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * rp<R>(P).gy;
+      const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * rp<R>(P).gx;
+      const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * rp<R>(P).gy;
       const R rt = rho1 + rho2;
       r1o = double(rho1);
       r2o = double(rho2);
@@ -130,7 +130,7 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
           R s = ldc<R>(gk + node);
 #pragma unroll
           for (int a = 1; a < 5; ++a) s += ldc<R>(gk + a * N + node);
-          c = double(R(P.shift_c[k]) + s);
+          c = double(rp<R>(P).shift_c[k] + s);
         }
         o_conc[k * N + node] = c;
       }
@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(BUD_THREADS) k_budget_partial(const DevInst* _
   for (long long node = lo + threadIdx.x; node < hi; node += blockDim.x) {
     const uint8_t t = T[node] & T_MASK;
     if (is_fluid(t)) {
-      const double r1 = double(R(P.shift_f[0]) + density_c<R>(F, N, node));
-      const double r2 = double(R(P.shift_f[1]) + density_c<R>(F + 9 * N, N, node));
+      const double r1 = double(rp<R>(P).shift_f[0] + density_c<R>(F, N, node));
+      const double r2 = double(rp<R>(P).shift_f[1] + density_c<R>(F + 9 * N, N, node));
       acc[0] = fmax(acc[0], r1);
       acc[1] += r1;
       acc[2] += r2;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(BUD_THREADS) k_budget_partial(const DevInst* _
         R s = ldc<R>(gk + node);
 #pragma unroll
         for (int a = 1; a < 5; ++a) s += ldc<R>(gk + a * N + node);
-        acc[3 + k] += double(R(P.shift_c[k]) + s);
+        acc[3 + k] += double(rp<R>(P).shift_c[k] + s);
       }
     }
     acc[3 + MAXS] += Ip->V[node];

@@ -50,7 +50,7 @@ __device__ __forceinline__ void conc_at(const TG* gin, int N, int node, const De
     R s = ld<R>(gk + node);
 #pragma unroll
     for (int a = 1; a < 5; ++a) s += ld<R>(gk + a * N + node);
-    C[k] = R(P.shift_c[k]) + s;
+    C[k] = rp<R>(P).shift_c[k] + s;
   }
 }
 
@@ -153,7 +153,7 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
                                             unsigned long long step, R theta, const uint8_t* s_t,
                                             const uint8_t* s_m, int eo) {
   const int node = y * P.nx + x;
-  const R sh1 = R(P.shift_f[0]), sh2 = R(P.shift_f[1]);
+  const R sh1 = rp<R>(P).shift_f[0], sh2 = rp<R>(P).shift_f[1];
   double a_, b_;
   reservoir_rho(P, t, step, t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, node, theta), a_, b_);
   const R r1 = R(a_), r2 = R(b_);
@@ -202,7 +202,7 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
     if (s_m[eo]) {
       R Cr[NS];
 #pragma unroll
-      for (int k = 0; k < NS; ++k) Cr[k] = R(P.conc_in[k]);
+      for (int k = 0; k < NS; ++k) Cr[k] = rp<R>(P).conc_in[k];
       if (t == T_OUTLET) {
         const int ew = eo - 1;
 #pragma unroll
@@ -212,13 +212,13 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
       }
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        const R Ja = R(P.Ja[k]);
+        const R Ja = rp<R>(P).Ja[k];
 #pragma unroll
         for (int a = 1; a < 5; ++a) {
           const int en = eo + EY(a) * EXT_X + EX(a);
           if (!(is_fluid(s_t[en]) && s_m[en])) continue;
           const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
-          const R geq = Ja * (Cr[k] - R(P.shift_c[k])) + R(0.5) * Cr[k] * eu;
+          const R geq = Ja * (Cr[k] - rp<R>(P).shift_c[k]) + R(0.5) * Cr[k] * eu;
           nbr(P, x, y, EX(a), EY(a), xn, yn);
           st<TG, R>(gout + (k * 5 + a) * N + yn * P.nx + xn, geq);
         }
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
     const uint8_t* __restrict__ tin = Ip->type[cur];
     uint8_t* __restrict__ tout = Ip->type[cur ^ 1];
     const R theta = R(0.5 * ord_dec(Ip->scal[S_MAX0 + cur]));
-    const R sh1 = R(P.shift_f[0]), sh2 = R(P.shift_f[1]);
+    const R sh1 = rp<R>(P).shift_f[0], sh2 = rp<R>(P).shift_f[1];
     // tiles whose ring is inside the domain need no wrap arithmetic
     const bool inner = tl.x0 >= 1 && tl.y0 >= 1 && tl.x0 + TX + 1 <= nx && tl.y0 + TY + 1 <= P.ny;
     R* sp = s_psi[buf];
@@ -394,18 +394,18 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
         if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
         if (EY(a) < 0) { spy -= vp; s2y -= v2; s1y -= v1; ssy -= vs; }
       }
-      const R G11 = R(P.G11), G12 = R(P.G12), G21 = R(P.G21), w1 = R(P.w_adh[0]), w2 = R(P.w_adh[1]);
-      const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * R(P.gx);
-      const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * R(P.gy);
-      const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * R(P.gx);
-      const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * R(P.gy);
+      const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0], w2 = rp<R>(P).w_adh[1];
+      const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * rp<R>(P).gx;
+      const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * rp<R>(P).gy;
+      const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * rp<R>(P).gx;
+      const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * rp<R>(P).gy;
       // ---- velocities (Eqs. 17-19)
-      const R it1 = R(P.inv_tau[0]), it2 = R(P.inv_tau[1]);
+      const R it1 = rp<R>(P).inv_tau[0], it2 = rp<R>(P).inv_tau[1];
       const R rden = rrcp<R>(rho1 * it1 + rho2 * it2);
       const R upx = (j1x * it1 + j2x * it2) * rden;
       const R upy = (j1y * it1 + j2y * it2) * rden;
-      const R q1 = rho1 != R(0) ? R(P.tau[0]) * rrcp<R>(rho1) : R(0);
-      const R q2 = rho2 != R(0) ? R(P.tau[1]) * rrcp<R>(rho2) : R(0);
+      const R q1 = rho1 != R(0) ? rp<R>(P).tau[0] * rrcp<R>(rho1) : R(0);
+      const R q2 = rho2 != R(0) ? rp<R>(P).tau[1] * rrcp<R>(rho2) : R(0);
       const R u1x = upx + F1x * q1, u1y = upy + F1y * q1;
       const R u2x = upx + F2x * q2, u2y = upy + F2y * q2;
       const R rrt = rrcp<R>(rho1 + rho2);
@@ -438,11 +438,11 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
             amend_marking<R, TF, TG, NS>(P, tin, fin, gin, N, x, y, appear, st_, sm_, eo, theta, dC, cb);
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
-              const R J0 = R(P.J0[k]), Ja = R(P.Ja[k]);
+              const R J0 = rp<R>(P).J0[k], Ja = rp<R>(P).Ja[k];
 #pragma unroll
               for (int a = 0; a < 5; ++a) {
                 const R ja = a == 0 ? J0 : Ja;
-                gs[k][a] = appear ? ja * (cb[k] + dC[k]) - ja * R(P.shift_c[k]) : gs[k][a] + ja * dC[k];
+                gs[k][a] = appear ? ja * (cb[k] + dC[k]) - ja * rp<R>(P).shift_c[k] : gs[k][a] + ja * dC[k];
               }
             }
           }
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
             R s = gs[k][0];
 #pragma unroll
             for (int a = 1; a < 5; ++a) s += gs[k][a];
-            C[k] = R(P.shift_c[k]) + s;
+            C[k] = rp<R>(P).shift_c[k] + s;
           }
           // homogeneous reactions (Eqs. 5a, 5c; sources Eqs. 27, 28)
           R CA = R(0), CB = R(0), CE = R(0), tot = R(0);
@@ -462,15 +462,14 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
             if (k == P.iE) CE = C[k];
             tot += C[k];
           }
-          if (P.iA == -2) CA = rmax<R>(R(0), R(P.c_total_per_rho1) * rho1 - tot);
-          R R1 = R(P.k1) * CA;
-          if (P.inv_Keq != 0.0)
-            R1 -= R(P.k1) * R(P.inv_Keq) * CB * rsqrt_<R>(rmax<R>(rho2 * R(P.inv_M_C), R(0)));
-          const R R3 = R(P.k3) * CB * CE;
+          if (P.iA == -2) CA = rmax<R>(R(0), rp<R>(P).c_total_per_rho1 * rho1 - tot);
+          R R1 = rp<R>(P).k1 * CA;
+          if (P.has_rev) R1 -= rp<R>(P).k1_inv_Keq * CB * rsqrt_<R>(rmax<R>(rho2 * rp<R>(P).inv_M_C, R(0)));
+          const R R3 = rp<R>(P).k3 * CB * CE;
 #pragma unroll
-          for (int k = 0; k < NS; ++k) Sk[k] = R(P.cR1[k]) * R1 + R(P.cR3[k]) * R3;
-          S1 = -R(P.gas_yield) * R1;
-          S2 = R(P.gas_yield) * R1;
+          for (int k = 0; k < NS; ++k) Sk[k] = rp<R>(P).cR1[k] * R1 + rp<R>(P).cR3[k] * R3;
+          S1 = -rp<R>(P).gas_yield * R1;
+          S2 = rp<R>(P).gas_yield * R1;
         }
       }
 
@@ -525,9 +524,9 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
             }
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
-              const R ja = a == 0 ? R(P.J0[k]) : R(P.Ja[k]);
-              const R geq = ja * (C[k] - R(P.shift_c[k])) + R(0.5) * C[k] * eu;
-              const R gst = gs[k][a] - (gs[k][a] - geq) * R(P.inv_tau_g[k]) + ja * Sk[k];
+              const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
+              const R geq = ja * (C[k] - rp<R>(P).shift_c[k]) + R(0.5) * C[k] * eu;
+              const R gst = gs[k][a] - (gs[k][a] - geq) * rp<R>(P).inv_tau_g[k] + ja * Sk[k];
               if (keep) st<TG, R>(gout + (k * 5 + slot) * N + dst, gst);
             }
           }
@@ -537,7 +536,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
           for (int k = 0; k < NS; ++k) {
 #pragma unroll
             for (int a = 0; a < 5; ++a)
-              st<TG, R>(gout + (k * 5 + a) * N + node, -(a == 0 ? R(P.J0[k]) : R(P.Ja[k])) * R(P.shift_c[k]));
+              st<TG, R>(gout + (k * 5 + a) * N + node, -(a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k]) * rp<R>(P).shift_c[k]);
           }
         }
       }

@@ -15,9 +15,16 @@ constexpr uint8_t T_MASK = 0x0F;     // low nibble: node type
 constexpr uint8_t T_NEW = 0x40;      // flag set by the amendment kernel: solid -> liquid this step
 constexpr uint8_t T_VANISH = 0x80;   // flag: liquid -> solid this step
 
-// Tile shape of the bulk kernels (one thread per interior node).
-constexpr int TX = 32;
-constexpr int TY = 8;
+// Tile shape of the bulk kernels (one thread per interior node); 16x16 measured
+// fastest of 32x8, 64x4, 32x16, 16x16 and 64x8 on the porous workload.
+#ifndef PSLBM_TX
+#define PSLBM_TX 16
+#endif
+#ifndef PSLBM_TY
+#define PSLBM_TY 16
+#endif
+constexpr int TX = PSLBM_TX;
+constexpr int TY = PSLBM_TY;
 constexpr int EXT_X = TX + 2;
 constexpr int EXT_Y = TY + 2;
 constexpr int EXT = EXT_X * EXT_Y;
@@ -43,10 +50,23 @@ constexpr int BUD_THREADS = 256;
 // Event codes written by the VOP kernel.
 enum { EV_NONE = 0, EV_DISSOLVE = 1, EV_OVERFLOW = 2 };   // overflow: code | (dir << 4)
 
+// Parameters used in arithmetic, stored in the compute precision so that no
+// kernel converts FP64 values at run time (FP64 runs at a small fraction of the
+// FP32 rate on GB300).  Reciprocals replace divisions where a parameter divides.
+template <class R>
+struct DevParamsR {
+  R tau[2], inv_tau[2], G11, G12, G21, a0, inv_rho10, inv_rho20, w_adh[2];
+  R eos_a, eos_b4, eos_RT, six_over_G11;
+  R gx, gy, shift_f[2], rho_fill[2];
+  R J0[MAXS], Ja[MAXS], inv_tau_g[MAXS], shift_c[MAXS], conc_in[MAXS], cR1[MAXS], cR3[MAXS];
+  R k1, k1_inv_Keq, k3, k2, k4, C_F_sat, gas_yield, inv_M_C, c_total_per_rho1;
+};
+
 struct DevParams {
   int nx, ny, px, py, ns;
   int iA, iB, iE, iF;
   int per_liq, per_gas, ramp;
+  int has_G11, has_rev, useB, useF;   // G11 != 0, inv_Keq != 0, R2 active, R4 active
   double tau[2], G11, G12, G21, a0, rho10, rho20, w_adh[2];
   double eos_a, eos_b, eos_R, eos_T;
   double gx, gy;
@@ -60,7 +80,13 @@ struct DevParams {
   unsigned long long seed;
   double rho_in_liq[2], rho_in_gas[2], rho_out[2], rho_out_gas[2];
   double conc_in[MAXS];
+  DevParamsR<float> rf;
+  DevParamsR<double> rd;
 };
+
+template <class R> __host__ __device__ __forceinline__ const DevParamsR<R>& rp(const DevParams& P);
+template <> __host__ __device__ __forceinline__ const DevParamsR<float>& rp<float>(const DevParams& P) { return P.rf; }
+template <> __host__ __device__ __forceinline__ const DevParamsR<double>& rp<double>(const DevParams& P) { return P.rd; }
 
 struct DevInst {
   DevParams P;
@@ -211,7 +237,7 @@ __device__ __forceinline__ bool liquid_at(const DevParams& P, const uint8_t* tin
                                           R theta) {
   uint8_t t = tin[node] & T_MASK;
   if (!is_fluid(t)) return false;
-  R rho1 = R(P.shift_f[0]) + density_shifted<R>(fin, (long long)N, node);
+  R rho1 = rp<R>(P).shift_f[0] + density_shifted<R>(fin, (long long)N, node);
   return rho1 > theta;
 }
 
@@ -224,13 +250,13 @@ __device__ __forceinline__ bool outlet_up_liquid(const DevParams& P, const uint8
   return liquid_at<R, TF>(P, tin, fin, N, yn * P.nx + xn, theta);
 }
 
-// Eq. 12 (C-S EOS) and the Eq. 13 square-root argument.
+// Eq. 12 (C-S EOS) and the Eq. 13 square-root argument 6/G11 (p - rho/3).
 template <class R> __device__ __forceinline__ R psi_arg(const DevParams& P, R rho) {
-  R eta = R(P.eos_b) * rho / R(4);
-  R om = R(1) - eta;
-  R p = rho * R(P.eos_R) * R(P.eos_T) * (R(1) + eta + eta * eta - eta * eta * eta) / (om * om * om) -
-        R(P.eos_a) * rho * rho;
-  return R(6) / R(P.G11) * (p - rho / R(3));
+  const DevParamsR<R>& Q = rp<R>(P);
+  const R eta = Q.eos_b4 * rho;
+  const R om = R(1) - eta;
+  const R p = rho * Q.eos_RT * (R(1) + eta + eta * eta - eta * eta * eta) / (om * om * om) - Q.eos_a * rho * rho;
+  return Q.six_over_G11 * (p - rho / R(3));
 }
 
 template <class R> __device__ __forceinline__ R rrcp(R v);
@@ -250,7 +276,8 @@ template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqr
 template <class R>
 __device__ __forceinline__ void potentials(const DevParams& P, R rho1, R rho2, R& psi, R& phi1, R& phi2,
                                            unsigned& status) {
-  if (P.G11 != 0.0) {
+  const DevParamsR<R>& Q = rp<R>(P);
+  if (P.has_G11) {
     R arg = psi_arg<R>(P, rho1);
     if (!(arg >= R(0))) {
       status |= (arg == arg) ? ST_EOS : ST_NONFINITE;
@@ -260,8 +287,30 @@ __device__ __forceinline__ void potentials(const DevParams& P, R rho1, R rho2, R
   } else {
     psi = R(0);
   }
-  phi1 = R(1) - rexp<R>(-rho2 / R(P.rho20));
-  phi2 = R(P.a0) - rexp<R>(-rho1 / R(P.rho10));
+  phi1 = R(1) - rexp<R>(-rho2 * Q.inv_rho20);
+  phi2 = Q.a0 - rexp<R>(-rho1 * Q.inv_rho10);
+}
+
+// Same as potentials(), with the parameters taken from a block already staged
+// in the compute precision (shared memory in the bulk kernel).
+template <class R>
+__device__ __forceinline__ void potentials_q(const DevParamsR<R>& Q, bool has_G11, R rho1, R rho2, R& psi, R& phi1,
+                                             R& phi2, unsigned& status) {
+  if (has_G11) {
+    const R eta = Q.eos_b4 * rho1;
+    const R om = R(1) - eta;
+    const R p = rho1 * Q.eos_RT * (R(1) + eta + eta * eta - eta * eta * eta) / (om * om * om) - Q.eos_a * rho1 * rho1;
+    R arg = Q.six_over_G11 * (p - rho1 / R(3));
+    if (!(arg >= R(0))) {
+      status |= (arg == arg) ? ST_EOS : ST_NONFINITE;
+      arg = R(0);
+    }
+    psi = rsqrt_<R>(arg);
+  } else {
+    psi = R(0);
+  }
+  phi1 = R(1) - rexp<R>(-rho2 * Q.inv_rho20);
+  phi2 = Q.a0 - rexp<R>(-rho1 * Q.inv_rho10);
 }
 
 // SplitMix64 output for a given state (Steele, Lea, Flood 2014).

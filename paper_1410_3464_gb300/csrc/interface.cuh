@@ -52,11 +52,11 @@ __global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles
       dirs[nl++] = b;
     }
     if (nl == 0) continue;
-    double sB = 0.0, sF = 0.0;
+    R sB = R(0), sF = R(0);
     if constexpr (NS > 0) {
       TG* gout = (TG*)Ip->g[cur ^ 1];
-      const bool useB = (t == T_SOLID_D) && P.iB >= 0 && P.k2 != 0.0;
-      const bool useF = P.iF >= 0 && P.k4 != 0.0;
+      const bool useB = (t == T_SOLID_D) && P.useB;
+      const bool useF = P.useF != 0;
 #pragma unroll
       for (int b = 1; b < 5; ++b) {
         const int nn = nbx[b - 1];
@@ -64,14 +64,14 @@ __global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles
         // the population that left nn toward this node was bounced into slot b of nn
         if (useB) {
           const int iB = P.iB;
-          const R Ja = R(P.Ja[iB]), sh = Ja * R(P.shift_c[iB]);
+          const R Ja = rp<R>(P).Ja[iB], sh = Ja * rp<R>(P).shift_c[iB];
           TG* slot = gout + (iB * 5 + b) * N + nn;
           const R out = ldc<R>(slot) + sh;
-          const R kap = R(P.k2) / (R(2) * Ja);
+          const R kap = rp<R>(P).k2 / (R(2) * Ja);
           const R bk = out * (R(1) - kap) / (R(1) + kap);
           const R q = out - bk;
           st<TG, R>(slot, bk - sh);
-          sB += double(q);
+          sB += q;
           if (P.iE >= 0) {
             TG* se = gout + (P.iE * 5 + b) * N + nn;
             st<TG, R>(se, ldc<R>(se) + q);
@@ -79,19 +79,20 @@ __global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles
         }
         if (useF) {
           const int iF = P.iF;
-          const R Ja = R(P.Ja[iF]), sh = Ja * R(P.shift_c[iF]);
+          const R Ja = rp<R>(P).Ja[iF], sh = Ja * rp<R>(P).shift_c[iF];
           TG* slot = gout + (iF * 5 + b) * N + nn;
           const R out = ldc<R>(slot) + sh;
-          const R kap = R(P.k4) / (R(2) * Ja);
-          const R bk = (out * (R(1) - kap) + R(P.k4) * R(P.C_F_sat)) / (R(1) + kap);
+          const R kap = rp<R>(P).k4 / (R(2) * Ja);
+          const R bk = (out * (R(1) - kap) + rp<R>(P).k4 * rp<R>(P).C_F_sat) / (R(1) + kap);
           st<TG, R>(slot, bk - sh);
-          sF += double(out - bk);
+          sF += out - bk;
         }
       }
     }
     double VD = Ip->V[node], VF = Ip->V[N + node];
-    if (t == T_SOLID_D) VD = VD - P.Vbar_D * sB;   // Eq. 33
-    VF = VF + P.Vbar_F * sF;                        // Eq. 35 (precipitation adds volume)
+    // volumes accumulate in FP64: per-step increments are far below FP32 resolution of V
+    if (t == T_SOLID_D) VD = VD - P.Vbar_D * double(sB);   // Eq. 33
+    VF = VF + P.Vbar_F * double(sF);                        // Eq. 35 (precipitation adds volume)
     if (VD < 0.0) VD = 0.0;
     const double total = VD + VF;
     int code = EV_NONE;
@@ -210,8 +211,8 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
       const long long nn = (long long)yn * P.nx + xn;
       const uint8_t tf = T[nn];
       if (surv_fluid(tf)) {
-        s1 += R(P.shift_f[0]) + density_c<R>(F, N, nn);
-        s2 += R(P.shift_f[1]) + density_c<R>(F + 9 * N, N, nn);
+        s1 += rp<R>(P).shift_f[0] + density_c<R>(F, N, nn);
+        s2 += rp<R>(P).shift_f[1] + density_c<R>(F + 9 * N, N, nn);
         ++nf;
       }
       if (surv_liquid(tf)) {
@@ -221,27 +222,27 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
           R c = ldc<R>(gk + nn);
 #pragma unroll
           for (int a = 1; a < 5; ++a) c += ldc<R>(gk + a * N + nn);
-          sc[k] += R(P.shift_c[k]) + c;
+          sc[k] += rp<R>(P).shift_c[k] + c;
         }
         ++nl;
       }
     }
-    const R r1 = nf ? s1 / R(nf) : R(P.rho_fill[0]);
-    const R r2 = nf ? s2 / R(nf) : R(P.rho_fill[1]);
+    const R r1 = nf ? s1 / R(nf) : rp<R>(P).rho_fill[0];
+    const R r2 = nf ? s2 / R(nf) : rp<R>(P).rho_fill[1];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const R w = w9<R>(a);
-      st<TF, R>(F + a * N + node, w * r1 - w * R(P.shift_f[0]));
-      st<TF, R>(F + (9 + a) * N + node, w * r2 - w * R(P.shift_f[1]));
+      st<TF, R>(F + a * N + node, w * r1 - w * rp<R>(P).shift_f[0]);
+      st<TF, R>(F + (9 + a) * N + node, w * r2 - w * rp<R>(P).shift_f[1]);
     }
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       const R c = nl ? sc[k] / R(nl) : R(0);
-      const R J0 = R(P.J0[k]), Ja = (R(1) - J0) / R(4);
+      const R J0 = rp<R>(P).J0[k], Ja = (R(1) - J0) / R(4);
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
         const R ja = a == 0 ? J0 : Ja;
-        st<TG, R>(G + ((long long)k * 5 + a) * N + node, ja * c - ja * R(P.shift_c[k]));
+        st<TG, R>(G + ((long long)k * 5 + a) * N + node, ja * c - ja * rp<R>(P).shift_c[k]);
       }
     }
   }
@@ -276,8 +277,8 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
         nf += surv_fluid(tz) ? 1 : 0;
         nl += surv_liquid(tz) ? 1 : 0;
       }
-      add1 += (R(P.shift_f[0]) + density_c<R>(F, N, w)) / R(nf);
-      add2 += (R(P.shift_f[1]) + density_c<R>(F + 9 * N, N, w)) / R(nf);
+      add1 += (rp<R>(P).shift_f[0] + density_c<R>(F, N, w)) / R(nf);
+      add2 += (rp<R>(P).shift_f[1] + density_c<R>(F + 9 * N, N, w)) / R(nf);
       if (nliq && nl) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
           R c = ldc<R>(gk + w);
 #pragma unroll
           for (int a = 1; a < 5; ++a) c += ldc<R>(gk + a * N + w);
-          addc[k] += (R(P.shift_c[k]) + c) / R(nl);
+          addc[k] += (rp<R>(P).shift_c[k] + c) / R(nl);
         }
       }
     }
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
     if (nliq) {
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
-        const R J0 = R(P.J0[k]), Ja = (R(1) - J0) / R(4);
+        const R J0 = rp<R>(P).J0[k], Ja = (R(1) - J0) / R(4);
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
           TG* p = G + ((long long)k * 5 + a) * N + n;

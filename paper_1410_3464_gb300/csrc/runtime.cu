@@ -151,6 +151,47 @@ std::string validate(const pslbm_params* p) {
   return "";
 }
 
+template <class R>
+void fill_r(DevParamsR<R>& q, const DevParams& P) {
+  for (int s = 0; s < 2; ++s) {
+    q.tau[s] = R(P.tau[s]);
+    q.inv_tau[s] = R(P.inv_tau[s]);
+    q.w_adh[s] = R(P.w_adh[s]);
+    q.shift_f[s] = R(P.shift_f[s]);
+    q.rho_fill[s] = R(P.rho_fill[s]);
+  }
+  q.G11 = R(P.G11);
+  q.G12 = R(P.G12);
+  q.G21 = R(P.G21);
+  q.a0 = R(P.a0);
+  q.inv_rho10 = R(1.0 / P.rho10);
+  q.inv_rho20 = R(1.0 / P.rho20);
+  q.eos_a = R(P.eos_a);
+  q.eos_b4 = R(P.eos_b / 4.0);
+  q.eos_RT = R(P.eos_R * P.eos_T);
+  q.six_over_G11 = R(P.G11 != 0.0 ? 6.0 / P.G11 : 0.0);
+  q.gx = R(P.gx);
+  q.gy = R(P.gy);
+  for (int k = 0; k < MAXS; ++k) {
+    q.J0[k] = R(P.J0[k]);
+    q.Ja[k] = R(P.Ja[k]);
+    q.inv_tau_g[k] = R(P.inv_tau_g[k]);
+    q.shift_c[k] = R(P.shift_c[k]);
+    q.conc_in[k] = R(P.conc_in[k]);
+    q.cR1[k] = R(P.cR1[k]);
+    q.cR3[k] = R(P.cR3[k]);
+  }
+  q.k1 = R(P.k1);
+  q.k1_inv_Keq = R(P.k1 * P.inv_Keq);
+  q.k3 = R(P.k3);
+  q.k2 = R(P.k2);
+  q.k4 = R(P.k4);
+  q.C_F_sat = R(P.C_F_sat);
+  q.gas_yield = R(P.gas_yield);
+  q.inv_M_C = R(P.inv_M_C);
+  q.c_total_per_rho1 = R(P.c_total_per_rho1);
+}
+
 DevParams to_dev(const pslbm_params* p) {
   DevParams P{};
   P.nx = p->nx;
@@ -213,6 +254,12 @@ DevParams to_dev(const pslbm_params* p) {
   P.Vbar_F = p->Vbar_F;
   P.V_split = p->V_split;
   P.seed = p->seed;
+  P.has_G11 = p->G11 != 0.0;
+  P.has_rev = p->inv_Keq != 0.0;
+  P.useB = p->idx_B >= 0 && p->k2 != 0.0;
+  P.useF = p->idx_F >= 0 && p->k4 != 0.0;
+  fill_r(P.rf, P);
+  fill_r(P.rd, P);
   return P;
 }
 
