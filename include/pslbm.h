@@ -167,6 +167,15 @@ pslbm_status pslbm_read_fields(pslbm_t h, uint32_t fields, void* const* out);
  * pslbm_step. */
 pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double* total_ms);
 
+/* Freeze the simulation once it has taken `limit` steps (limit < 0: no limit).
+ * Steps requested beyond the limit leave the state unchanged, so simulations
+ * with different step budgets can share one batch.  Synchronises. */
+pslbm_status pslbm_set_step_limit(pslbm_t h, int64_t limit);
+
+/* Device bytes pslbm_create would allocate for this parameter set (excluding
+ * the read-back scratch of pslbm_read_fields). */
+pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes);
+
 /* Number of steps taken and lattice size. */
 pslbm_status pslbm_info(pslbm_t h, int64_t* steps, int32_t* nx, int32_t* ny, int32_t* n_species);
 
@@ -209,6 +218,46 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
 pslbm_status pslbm_batch_step(pslbm_batch_t b, int64_t n);
 pslbm_status pslbm_batch_sync(pslbm_batch_t b);
 pslbm_status pslbm_batch_destroy(pslbm_batch_t b);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of simulation requests.  Requests queue on the host;
+ * each pslbm_server_advance() admits queued requests in arrival order while
+ * the device-memory estimate of the resident simulations stays within
+ * hbm_budget_bytes (and their count within max_active), re-packs the resident
+ * simulations into batches when the set changed, advances them by chunk_steps
+ * steps (a simulation is frozen at its step budget), and retires requests that
+ * reached their step budget or whose total solid volume changed by at least
+ * their stop fraction (checked after each chunk).  Retired requests keep their
+ * final budget (and their fields if asked) on the host until released. */
+typedef struct pslbm_server_s* pslbm_server_t;
+typedef struct {
+    uint32_t struct_size;          /* sizeof(pslbm_server_config) */
+    int32_t precision;             /* pslbm_precision of every resident simulation */
+    uint64_t hbm_budget_bytes;     /* admission budget of device memory */
+    int32_t chunk_steps;           /* steps per scheduling chunk (>= 1) */
+    int32_t max_active;            /* resident simulation cap (>= 1) */
+} pslbm_server_config;
+enum { PSLBM_REQ_QUEUED = 0, PSLBM_REQ_ACTIVE = 1, PSLBM_REQ_DONE = 2, PSLBM_REQ_FAILED = 3 };
+
+pslbm_status pslbm_server_create(const pslbm_server_config* config, pslbm_server_t* out);
+/* Queue a request (inputs as in pslbm_create, copied; the server's precision
+ * replaces p->precision).  step_budget >= 1; stop_dv_frac > 0 also retires the
+ * request once |sum V - sum V(0)| >= stop_dv_frac * sum V(0); keep_fields != 0
+ * keeps rho1, rho2, ux, uy, conc, type and vol of the final state for fetch. */
+pslbm_status pslbm_server_submit(pslbm_server_t s, const uint8_t* mask, const double* rho1, const double* rho2,
+                                 const double* conc, const double* vol, const pslbm_params* p,
+                                 int64_t step_budget, double stop_dv_frac, int32_t keep_fields, uint64_t* req_id);
+/* Run one scheduling chunk; reports resident, queued and just-retired counts.  Synchronises. */
+pslbm_status pslbm_server_advance(pslbm_server_t s, int32_t* n_active, int32_t* n_queued, int32_t* n_done);
+/* State (PSLBM_REQ_*), steps taken, and for a finished request its final
+ * budget (6 + n_species doubles, layout of PSLBM_F_BUDGET) into budget_out (nullable). */
+pslbm_status pslbm_server_poll(pslbm_server_t s, uint64_t req_id, int32_t* state, int64_t* steps_done,
+                               double* budget_out);
+/* Kept fields of a finished request (bits PSLBM_F_RHO1 .. PSLBM_F_VOL, buffers in bit order). */
+pslbm_status pslbm_server_fetch(pslbm_server_t s, uint64_t req_id, uint32_t fields, void* const* out);
+pslbm_status pslbm_server_release(pslbm_server_t s, uint64_t req_id);
+const char* pslbm_server_last_error(pslbm_server_t s);
+pslbm_status pslbm_server_destroy(pslbm_server_t s);
 
 #ifdef __cplusplus
 }

@@ -260,13 +260,19 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
   TileTypes tt;
   if (ti < ntiles) tt = load_types(tiles, insts, ti, tid);
 
-  for (; ti < ntiles; ti += gridDim.x, buf ^= 1) {
+  for (; ti < ntiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const DevInst* Ip = insts + tl.inst;
     const DevParams& P = Ip->P;
     const int N = (int)Ip->N;
     const int nx = P.nx;
     const unsigned long long step = Ip->scal[S_STEP];
+    if (step >= Ip->scal[S_LIMIT]) {
+      // frozen instance: keep the type prefetch in step with the tile walk; the
+      // stage buffer is not toggled, so no barrier is skipped for it
+      if (ti + (int)gridDim.x < ntiles) tt = load_types(tiles, insts, ti + gridDim.x, tid);
+      continue;
+    }
     const int cur = int(step & 1ULL);
     const TF* __restrict__ fin = (const TF*)Ip->f[cur];
     TF* __restrict__ fout = (TF*)Ip->f[cur ^ 1];
@@ -558,6 +564,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
       }
       if (status) atomicOr(&Ip->scal[S_STATUS], (unsigned long long)status);
     }
+    buf ^= 1;
   }
 }
 

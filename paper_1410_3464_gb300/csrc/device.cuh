@@ -38,6 +38,7 @@ enum {
   S_MAX1 = 2,      // slot for odd steps
   S_STATUS = 3,    // error bits
   S_NEVENT = 4,    // events recorded by the VOP kernel this step
+  S_LIMIT = 5,     // step limit: an instance at or past it is frozen (kernels skip it)
   S_NSCAL = 8
 };
 enum { ST_NONFINITE = 1, ST_EOS = 2, ST_EVOVERFLOW = 4 };

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles
     if (x >= P.nx || y >= P.ny) continue;
     const int N = (int)Ip->N;
     const unsigned long long step = Ip->scal[S_STEP];
+    if (step >= Ip->scal[S_LIMIT]) continue;   // frozen instance
     const int cur = int(step & 1ULL);
     uint8_t* tnew = Ip->type[cur ^ 1];
     const int node = y * P.nx + x;
@@ -139,6 +140,7 @@ template <class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ insts) {
   const DevInst* Ip = insts + blockIdx.x;
   const unsigned long long step = Ip->scal[S_STEP];
+  if (step >= Ip->scal[S_LIMIT]) return;   // frozen instance
   const unsigned long long nev_raw = Ip->scal[S_NEVENT];
   if (nev_raw == 0) {
     if (threadIdx.x == 0) finish_step(Ip, step);

@@ -434,6 +434,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
     if (e == cudaSuccess) e = cudaMemsetAsync(I.evt, 0, (size_t)N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.claim, 0, (size_t)N * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.scal, 0, S_NSCAL * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.scal + S_LIMIT, 0xff, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.f[1], 0, (size_t)N * 18 * fsize(p->precision), s);
     if (e == cudaSuccess && ns) e = cudaMemsetAsync(I.g[1], 0, (size_t)N * 5 * ns * gsize(p->precision), s);
     if (e == cudaSuccess) {
@@ -556,6 +557,27 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
   for (int k = 0; k < 3; ++k) kernel_ms[k] = acc[k] / double(n);
   if (total_ms) *total_ms = tot / double(n);
   return device_status(h);
+}
+
+pslbm_status pslbm_set_step_limit(pslbm_t h, int64_t limit) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (h->sticky) return h->sticky;
+  const unsigned long long v = limit < 0 ? ~0ULL : (unsigned long long)limit;
+  CK(h, cudaMemcpyAsync(h->h.scal + S_LIMIT, &v, sizeof v, cudaMemcpyHostToDevice, lib_stream()));
+  CK(h, cudaStreamSynchronize(lib_stream()));
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes) {
+  if (!bytes) return fail(nullptr, PSLBM_ERR_PARAM, "bytes is NULL");
+  std::string v = validate(p);
+  if (!v.empty()) return fail(nullptr, PSLBM_ERR_PARAM, v);
+  const uint64_t N = (uint64_t)p->nx * (uint64_t)p->ny;
+  const uint64_t per = 2 * 18 * fsize(p->precision) + 2 * 5 * (uint64_t)p->n_species * gsize(p->precision) +
+                       2 /*types*/ + 16 /*V*/ + 1 /*events*/ + 8 /*excess*/ + 8 /*event lists*/ + 4 /*claims*/;
+  const uint64_t tiles = ((uint64_t)(p->nx + TX - 1) / TX) * ((uint64_t)(p->ny + TY - 1) / TY);
+  *bytes = N * per + tiles * sizeof(Tile) + sizeof(DevInst) + S_NSCAL * 8 + 12 * 16;
+  return PSLBM_OK;
 }
 
 pslbm_status pslbm_sync(pslbm_t h) {

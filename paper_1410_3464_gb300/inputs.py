@@ -219,3 +219,50 @@ def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
         p.update(inlet_period_liq=int(slug[0]), inlet_period_gas=int(slug[1]))
     conc = np.zeros((3, ny, nx))
     return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
+
+
+def _log_uniform(u, lo, hi):
+    return math.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))
+
+
+def request_stream(n, seed=5, size_range=(128, 2048), budget_range=(1000, 50000), rate_range=(1e-6, 1e-1),
+                   porosity_range=(0.4, 0.8), stop_fraction=0.05, mean_interarrival=1.0, multiple=16):
+    """Seeded stream of simulation requests: Poisson arrivals (exponential
+    inter-arrival times with the given mean, in seconds), lattice sides
+    log-uniform in `size_range` (rounded to a multiple of `multiple`), porosity
+    uniform, each of k1, k3, k2, k4 log-uniform in `rate_range` (k2, k4 capped
+    below (1 - J0)/2 = 1/3), step budget log-uniform (integer), half of the
+    requests also stopping once the total solid volume changed by
+    `stop_fraction`.  Returns a list of dicts (arrival, nx, ny, seed, porosity,
+    rates, step_budget, stop_dv)."""
+    rng = _splitmix64_stream(seed * 1000003 + 11)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += -mean_interarrival * math.log(max(1e-300, 1.0 - next(rng)))
+        nx = int(round(_log_uniform(next(rng), *size_range) / multiple)) * multiple
+        ny = int(round(_log_uniform(next(rng), *size_range) / multiple)) * multiple
+        nx, ny = max(nx, 64), max(ny, 64)
+        por = porosity_range[0] + next(rng) * (porosity_range[1] - porosity_range[0])
+        k1, k3, k2, k4 = (_log_uniform(next(rng), *rate_range) for _ in range(4))
+        k2, k4 = min(k2, 0.33), min(k4, 0.33)
+        budget = int(_log_uniform(next(rng), *budget_range))
+        stop = stop_fraction if next(rng) < 0.5 else 0.0
+        out.append(dict(arrival=t, nx=nx, ny=ny, seed=seed * 100000 + i, porosity=por,
+                        rates=(k1, k3, k2, k4), step_budget=budget, stop_dv=stop))
+    return out
+
+
+def request_scene(req):
+    """The porous-medium scene of one request of request_stream().  R1 turns
+    liquid mass into gas (Eq. 27); its rate is capped at 1e-4 so that the
+    liquid does not vaporise within the step budget.  The inlet overpressure
+    scales with the channel length so the driving gradient is the same for
+    every size."""
+    k1, k3, k2, k4 = req["rates"]
+    k1 = min(k1, 1e-4)
+    rmax = max(4.0, min(24.0, min(req["nx"], req["ny"]) / 6.0))
+    # same inlet pressure gradient as the 1024-node-long channel at 1 % overpressure
+    over = 1.0 + 0.01 * req["nx"] / 1024.0
+    return porous_discs(nx=req["nx"], ny=req["ny"], seed=req["seed"], porosity=req["porosity"],
+                        rmin=min(8.0, rmax / 2), rmax=rmax, k1=k1, k3=k3, k2=k2, k4=k4, overpressure=over)

@@ -26,7 +26,9 @@ EXPORTS = ["pslbm_get_stream", "pslbm_set_stream", "pslbm_create", "pslbm_step",
            "pslbm_profile_step",
            "pslbm_read_fields", "pslbm_info", "pslbm_device_bytes", "pslbm_destroy", "pslbm_last_error",
            "pslbm_batch_create", "pslbm_batch_step", "pslbm_batch_sync", "pslbm_batch_destroy",
-           "pslbm_budget_device_noalloc"]
+           "pslbm_budget_device_noalloc", "pslbm_set_step_limit", "pslbm_estimate_device_bytes",
+           "pslbm_server_create", "pslbm_server_submit", "pslbm_server_advance", "pslbm_server_poll",
+           "pslbm_server_fetch", "pslbm_server_release", "pslbm_server_last_error", "pslbm_server_destroy"]
 
 _D2 = C.c_double * 2
 _DS = C.c_double * MAX_SPECIES
@@ -75,6 +77,15 @@ def params_from_dict(d, precision=FP64):
     return p
 
 
+class ServerConfig(C.Structure):
+    """Mirror of pslbm_server_config."""
+    _fields_ = [("struct_size", C.c_uint32), ("precision", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
+                ("chunk_steps", C.c_int32), ("max_active", C.c_int32)]
+
+
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
 class PslbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -110,9 +121,21 @@ def load():
     lib.pslbm_batch_sync.argtypes = [vp]
     lib.pslbm_batch_destroy.argtypes = [vp]
     lib.pslbm_budget_device_noalloc.argtypes = [vp, vp]
+    lib.pslbm_set_step_limit.argtypes = [vp, i64]
+    lib.pslbm_estimate_device_bytes.argtypes = [C.POINTER(Params), C.POINTER(C.c_uint64)]
+    lib.pslbm_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(vp)]
+    lib.pslbm_server_submit.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(Params), i64, C.c_double, i32,
+                                        C.POINTER(C.c_uint64)]
+    lib.pslbm_server_advance.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    lib.pslbm_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(i32), C.POINTER(i64), vp]
+    lib.pslbm_server_fetch.argtypes = [vp, C.c_uint64, u32, C.POINTER(vp)]
+    lib.pslbm_server_release.argtypes = [vp, C.c_uint64]
+    lib.pslbm_server_last_error.argtypes = [vp]
+    lib.pslbm_server_last_error.restype = C.c_char_p
+    lib.pslbm_server_destroy.argtypes = [vp]
     for name in EXPORTS:
         fn = getattr(lib, name)
-        if name not in ("pslbm_get_stream", "pslbm_last_error"):
+        if name not in ("pslbm_get_stream", "pslbm_last_error", "pslbm_server_last_error"):
             fn.restype = C.c_int
     _lib = lib
     return lib
@@ -172,6 +195,9 @@ class Simulation:
         t = C.c_double()
         _check(load().pslbm_profile_step(self.h, int(n), k, C.byref(t)), self.h)
         return dict(bulk=k[0], vop=k[1], amend=k[2]), t.value
+
+    def set_step_limit(self, limit):
+        _check(load().pslbm_set_step_limit(self.h, int(limit)), self.h)
 
     def steps(self):
         t = C.c_int64()
@@ -253,6 +279,101 @@ class Batch:
         if getattr(self, "b", None):
             load().pslbm_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_device_bytes(params, precision=None):
+    d = dict(params)
+    if precision is not None:
+        d["precision"] = precision
+    prm = params_from_dict(d)
+    b = C.c_uint64()
+    _check(load().pslbm_estimate_device_bytes(C.byref(prm), C.byref(b)))
+    return int(b.value)
+
+
+class Server:
+    """Continuous-batching request server (pslbm_server_*)."""
+
+    def __init__(self, precision=FP32, hbm_budget_bytes=150 * 10**9, chunk_steps=200, max_active=1024):
+        lib = load()
+        cfg = ServerConfig()
+        cfg.struct_size = C.sizeof(ServerConfig)
+        cfg.precision = int(precision)
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.chunk_steps = int(chunk_steps)
+        cfg.max_active = int(max_active)
+        s = C.c_void_p()
+        st = lib.pslbm_server_create(C.byref(cfg), C.byref(s))
+        if st != 0:
+            raise PslbmError(st, "server create failed")
+        self.s = s
+        self._ns = {}
+
+    def _check(self, st):
+        if st != 0:
+            raise PslbmError(st, load().pslbm_server_last_error(self.s).decode(errors="replace"))
+
+    def submit(self, mask, params, rho1, rho2, conc=None, vol=None, step_budget=1000, stop_dv=0.0,
+               keep_fields=False):
+        prm = params_from_dict(dict(params))
+        shape = (prm.ny, prm.nx)
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(shape))
+        r1 = np.ascontiguousarray(np.asarray(rho1, dtype=np.float64).reshape(shape))
+        r2 = np.ascontiguousarray(np.asarray(rho2, dtype=np.float64).reshape(shape))
+        c = None if conc is None or prm.n_species == 0 else np.ascontiguousarray(
+            np.asarray(conc, dtype=np.float64).reshape((prm.n_species,) + shape))
+        v = None if vol is None else np.ascontiguousarray(np.asarray(vol, dtype=np.float64).reshape((2,) + shape))
+        rid = C.c_uint64()
+        self._check(load().pslbm_server_submit(self.s, _ptr(m), _ptr(r1), _ptr(r2), _ptr(c), _ptr(v), C.byref(prm),
+                                               int(step_budget), float(stop_dv), int(bool(keep_fields)),
+                                               C.byref(rid)))
+        self._ns[rid.value] = (prm.n_species, prm.nx, prm.ny)
+        return rid.value
+
+    def advance(self):
+        a, q, d = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(load().pslbm_server_advance(self.s, C.byref(a), C.byref(q), C.byref(d)))
+        return a.value, q.value, d.value
+
+    def poll(self, rid):
+        ns = self._ns[rid][0]
+        st, n = C.c_int32(), C.c_int64()
+        b = np.zeros(6 + ns)
+        self._check(load().pslbm_server_poll(self.s, int(rid), C.byref(st), C.byref(n), b.ctypes.data_as(C.c_void_p)))
+        return st.value, n.value, (b if st.value == REQ_DONE else None)
+
+    def fetch(self, rid):
+        ns, nx, ny = self._ns[rid]
+        shape = (ny, nx)
+        spec = [(F_RHO1, "rho1", np.float64, shape), (F_RHO2, "rho2", np.float64, shape),
+                (F_UX, "ux", np.float64, shape), (F_UY, "uy", np.float64, shape),
+                (F_CONC, "conc", np.float64, (ns,) + shape), (F_TYPE, "type", np.uint8, shape),
+                (F_VOL, "vol", np.float64, (2,) + shape)]
+        if ns == 0:
+            spec = [s for s in spec if s[0] != F_CONC]
+        bits, outs, ptrs = 0, {}, []
+        for bit, name, dt, shp in spec:
+            a = np.zeros(shp, dtype=dt)
+            outs[name] = a
+            ptrs.append(a.ctypes.data_as(C.c_void_p))
+            bits |= bit
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        self._check(load().pslbm_server_fetch(self.s, int(rid), bits, arr))
+        return outs
+
+    def release(self, rid):
+        self._check(load().pslbm_server_release(self.s, int(rid)))
+
+    def close(self):
+        if getattr(self, "s", None):
+            load().pslbm_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:
