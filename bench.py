@@ -191,6 +191,7 @@ def ours_arm(args):
     stream = torch.cuda.ExternalStream(pslbm.get_stream())
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     sim = pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"], precision=prec)
+    sim.step(10)          # the first long step call times both tile shapes and keeps the faster
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
@@ -238,6 +239,7 @@ def ours_arm(args):
         pj = json.load(open(PROFILE_JSON))
         if pj.get("source_hash") == kernel_source_hash():
             traffic = pj.get("dram_bytes_per_launch")
+    tshape = sim.tile_shape()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_bulk", "bytes_per_launch": bytes_per_launch,
                 "kernel_ms": bulk_ms, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
@@ -251,7 +253,8 @@ def ours_arm(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "nx": WORKLOAD["nx"], "ny": WORKLOAD["ny"],
                        "fluid_nodes": n_fluid, "liquid_nodes": n_liq, "precision": args.precision,
-                       "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
+                       "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
+                       "tile": f"{tshape[0]}x{tshape[1]}"},
             "roofline": roofline,
             "kernel_ms": {k: statistics.mean(v) for k, v in kern.items()},
             "gpu_launches": 3 * args.steps}

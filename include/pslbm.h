@@ -176,6 +176,13 @@ pslbm_status pslbm_set_step_limit(pslbm_t h, int64_t limit);
  * the read-back scratch of pslbm_read_fields). */
 pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes);
 
+/* Tile shape of the step kernels: 16x16 or 32x8 nodes per 256-thread block.
+ * (0, 0), the default, lets the next step call of at least 9 steps time both
+ * shapes on its first 8 steps and keep the faster; the results do not depend on
+ * the shape.  tuned reports whether a shape has been chosen. */
+pslbm_status pslbm_set_tile_shape(pslbm_t h, int32_t tile_x, int32_t tile_y);
+pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, int32_t* tuned);
+
 /* Number of steps taken and lattice size. */
 pslbm_status pslbm_info(pslbm_t h, int64_t* steps, int32_t* nx, int32_t* ny, int32_t* n_species);
 
@@ -212,11 +219,13 @@ pslbm_status pslbm_budget_device_noalloc(pslbm_t h, double* out);
  * A batch steps several simulations (same precision and species count) in
  * one launch per kernel over a packed list of tiles of all members.  The
  * members stay valid handles; they must not be stepped on their own while
- * the batch exists.  tile_x, tile_y choose the tile shape (0: automatic). */
+ * the batch exists.  tile_x, tile_y choose the tile shape (16x16 or 32x8;
+ * 0, 0: time both on the first steps and keep the faster). */
 pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_x, int32_t tile_y,
                                 pslbm_batch_t* out);
 pslbm_status pslbm_batch_step(pslbm_batch_t b, int64_t n);
 pslbm_status pslbm_batch_sync(pslbm_batch_t b);
+pslbm_status pslbm_batch_get_tile_shape(pslbm_batch_t b, int32_t* tile_x, int32_t* tile_y, int32_t* tuned);
 pslbm_status pslbm_batch_destroy(pslbm_batch_t b);
 
 /* ---------------------------------------------------------------- serving

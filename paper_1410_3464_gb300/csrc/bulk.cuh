@@ -25,20 +25,21 @@
 
 namespace pslbm {
 
-// Ring position r (0..RING-1) -> ext coordinates.
+// Ring position r (0..SH::RING-1) -> ext coordinates.
+template <class SH>
 __device__ __forceinline__ void ring_pos(int r, int& ex, int& ey) {
-  if (r < EXT_X) {
+  if (r < SH::EXT_X) {
     ex = r;
     ey = 0;
-  } else if (r < 2 * EXT_X) {
-    ex = r - EXT_X;
-    ey = EXT_Y - 1;
-  } else if (r < 2 * EXT_X + (EXT_Y - 2)) {
+  } else if (r < 2 * SH::EXT_X) {
+    ex = r - SH::EXT_X;
+    ey = SH::EXT_Y - 1;
+  } else if (r < 2 * SH::EXT_X + (SH::EXT_Y - 2)) {
     ex = 0;
-    ey = 1 + (r - 2 * EXT_X);
+    ey = 1 + (r - 2 * SH::EXT_X);
   } else {
-    ex = EXT_X - 1;
-    ey = 1 + (r - 2 * EXT_X - (EXT_Y - 2));
+    ex = SH::EXT_X - 1;
+    ey = 1 + (r - 2 * SH::EXT_X - (SH::EXT_Y - 2));
   }
 }
 
@@ -67,26 +68,27 @@ __device__ __forceinline__ uint8_t ext_type(const DevParams& P, const uint8_t* t
   return tin[idx] & T_MASK;
 }
 
-// Types of one tile for this thread: its own ext position and (tid < RING)
+// Types of one tile for this thread: its own ext position and (tid < SH::RING)
 // one ring position.
 struct TileTypes {
   uint8_t own, ring;
   int own_idx, ring_idx;
 };
 
+template <class SH>
 __device__ __forceinline__ TileTypes load_types(const Tile* tiles, const DevInst* insts, int ti, int tid) {
   TileTypes tt;
   const Tile tl = tiles[ti];
   const DevInst* Ip = insts + tl.inst;
   const int cur = int(Ip->scal[S_STEP] & 1ULL);
   const uint8_t* tin = Ip->type[cur];
-  const int tx = tid % TX, ty = tid / TX;
+  const int tx = tid % SH::TX, ty = tid / SH::TX;
   tt.own = ext_type(Ip->P, tin, tl.x0, tl.y0, tx + 1, ty + 1, tt.own_idx);
   tt.ring = T_WALL;
   tt.ring_idx = -1;
-  if (tid < RING) {
+  if (tid < SH::RING) {
     int ex, ey;
-    ring_pos(tid, ex, ey);
+    ring_pos<SH>(tid, ex, ey);
     tt.ring = ext_type(Ip->P, tin, tl.x0, tl.y0, ex, ey, tt.ring_idx);
   }
   return tt;
@@ -105,7 +107,7 @@ static __device__ __noinline__ int nbr_index(const DevParams& P, int x, int y, i
 // gas) neighbours, each giving C / (number of its liquid neighbours); for an
 // appearing (gas -> liquid) node, cb[k] receives the mean C of its surviving
 // liquid neighbours (0 if none).
-template <class R, class TF, class TG, int NS>
+template <class SH, class R, class TF, class TG, int NS>
 __device__ __noinline__ void amend_marking(const DevParams& P, const uint8_t* tin, const TF* fin, const TG* gin,
                                            int N, int x, int y, bool appear, const uint8_t* s_t,
                                            const uint8_t* s_m, int eo, R theta, R* dC, R* cb) {
@@ -115,7 +117,7 @@ __device__ __noinline__ void amend_marking(const DevParams& P, const uint8_t* ti
   int nsrc = 0;
 #pragma unroll
   for (int b = 1; b < 5; ++b) {
-    const int en = eo + EY(b) * EXT_X + EX(b);
+    const int en = eo + EY(b) * SH::EXT_X + EX(b);
     int xn, yn;
     if (!nbr(P, x, y, EX(b), EY(b), xn, yn)) continue;
     const int nn = yn * P.nx + xn;
@@ -147,7 +149,7 @@ __device__ __noinline__ void amend_marking(const DevParams& P, const uint8_t* ti
 // Reservoir node: push its equilibrium state (densities of reservoir_rho,
 // velocity of the node next to it along x) into its fluid neighbours, and the
 // solute equilibrium into its liquid neighbours when it is itself liquid.
-template <class R, class TF, class TG, int NS>
+template <class SH, class R, class TF, class TG, int NS>
 __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* tin, const TF* fin, const TG* gin,
                                             TF* fout, TG* gout, int N, int x, int y, uint8_t t,
                                             unsigned long long step, R theta, const uint8_t* s_t,
@@ -189,7 +191,7 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
     TF* fo = fout + s * 9 * N;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
-      const int en = eo + EY(a) * EXT_X + EX(a);
+      const int en = eo + EY(a) * SH::EXT_X + EX(a);
       if (!is_fluid(s_t[en])) continue;
       const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
       const R w = w9<R>(a);
@@ -215,7 +217,7 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
         const R Ja = rp<R>(P).Ja[k];
 #pragma unroll
         for (int a = 1; a < 5; ++a) {
-          const int en = eo + EY(a) * EXT_X + EX(a);
+          const int en = eo + EY(a) * SH::EXT_X + EX(a);
           if (!(is_fluid(s_t[en]) && s_m[en])) continue;
           const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
           const R geq = Ja * (Cr[k] - rp<R>(P).shift_c[k]) + R(0.5) * Cr[k] * eu;
@@ -238,27 +240,27 @@ constexpr int bulk_min_blocks() {
   return sizeof(R) == 8 ? 2 : PSLBM_BULK_MINB;
 }
 
-template <class TF, class TG, class R, int NS>
+template <class SH, class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const Tile* __restrict__ tiles, int ntiles,
                                                                          const DevInst* __restrict__ insts) {
-  __shared__ R s_psi[2][EXT], s_phi1[2][EXT], s_phi2[2][EXT];
-  __shared__ uint8_t s_t[2][EXT], s_m[2][EXT];
+  __shared__ R s_psi[2][SH::EXT], s_phi1[2][SH::EXT], s_phi2[2][SH::EXT];
+  __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int tx = tid % TX, ty = tid / TX;
-  const int eo = (ty + 1) * EXT_X + (tx + 1);
+  const int tx = tid % SH::TX, ty = tid / SH::TX;
+  const int eo = (ty + 1) * SH::EXT_X + (tx + 1);
   int er = -1;
-  if (tid < RING) {
+  if (tid < SH::RING) {
     int ex, ey;
-    ring_pos(tid, ex, ey);
-    er = ey * EXT_X + ex;
+    ring_pos<SH>(tid, ex, ey);
+    er = ey * SH::EXT_X + ex;
   }
 
   int ti = blockIdx.x;
   int buf = 0;
   TileTypes tt;
-  if (ti < ntiles) tt = load_types(tiles, insts, ti, tid);
+  if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, tid);
 
   for (; ti < ntiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
     if (step >= Ip->scal[S_LIMIT]) {
       // frozen instance: keep the type prefetch in step with the tile walk; the
       // stage buffer is not toggled, so no barrier is skipped for it
-      if (ti + (int)gridDim.x < ntiles) tt = load_types(tiles, insts, ti + gridDim.x, tid);
+      if (ti + (int)gridDim.x < ntiles) tt = load_types<SH>(tiles, insts, ti + gridDim.x, tid);
       continue;
     }
     const int cur = int(step & 1ULL);
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
     const R theta = R(0.5 * ord_dec(Ip->scal[S_MAX0 + cur]));
     const R sh1 = rp<R>(P).shift_f[0], sh2 = rp<R>(P).shift_f[1];
     // tiles whose ring is inside the domain need no wrap arithmetic
-    const bool inner = tl.x0 >= 1 && tl.y0 >= 1 && tl.x0 + TX + 1 <= nx && tl.y0 + TY + 1 <= P.ny;
+    const bool inner = tl.x0 >= 1 && tl.y0 >= 1 && tl.x0 + SH::TX + 1 <= nx && tl.y0 + SH::TY + 1 <= P.ny;
     R* sp = s_psi[buf];
     R* sq1 = s_phi1[buf];
     R* sq2 = s_phi2[buf];
@@ -318,12 +320,12 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
       }
     }
     R r1r = R(0), r2r = R(0);
-    if (tid < RING && is_fluid(ring_t)) {
+    if (tid < SH::RING && is_fluid(ring_t)) {
       r1r = sh1 + density_shifted<R>(fin, (long long)N, ring_idx);
       r2r = sh2 + density_shifted<R>(fin + 9 * N, (long long)N, ring_idx);
     }
     // prefetch the next tile's node types
-    if (ti + (int)gridDim.x < ntiles) tt = load_types(tiles, insts, ti + gridDim.x, tid);
+    if (ti + (int)gridDim.x < ntiles) tt = load_types<SH>(tiles, insts, ti + gridDim.x, tid);
 
     // ---- moments of the own node (Eq. 9), potentials -> shared
     R rho1 = R(0), rho2 = R(0), d1 = R(0), d2 = R(0), j1x = R(0), j1y = R(0), j2x = R(0), j2y = R(0);
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
       st_[eo] = own_t;
       sm_[eo] = (is_live(own_t) && r1 > theta) ? 1 : 0;
     }
-    if (tid < RING) {
+    if (tid < SH::RING) {
       R r1 = r1r, r2 = r2r;
       if (is_res(ring_t)) {
         double a, b;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
       R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
 #pragma unroll
       for (int a = 1; a < 9; ++a) {
-        const int en = eo + EY(a) * EXT_X + EX(a);
+        const int en = eo + EY(a) * SH::EXT_X + EX(a);
         const bool lv = is_live(st_[en]);
         const R w = wf<R>(a);
         const R vp = w * (lv ? sp[en] : psc);
@@ -436,12 +438,12 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
           bool vnb = false;
 #pragma unroll
           for (int b = 1; b < 5; ++b) {
-            const int en = eo + EY(b) * EXT_X + EX(b);
+            const int en = eo + EY(b) * SH::EXT_X + EX(b);
             vnb |= (st_[en] == T_LIQUID && sm_[en] == 0);
           }
           if (appear || vnb) {
             R dC[NS], cb[NS];
-            amend_marking<R, TF, TG, NS>(P, tin, fin, gin, N, x, y, appear, st_, sm_, eo, theta, dC, cb);
+            amend_marking<SH, R, TF, TG, NS>(P, tin, fin, gin, N, x, y, appear, st_, sm_, eo, theta, dC, cb);
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
               const R J0 = rp<R>(P).J0[k], Ja = rp<R>(P).Ja[k];
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
             st<TF, R>(fo + node, fs);
             continue;
           }
-          const uint8_t tn = st_[eo + EY(a) * EXT_X + EX(a)];
+          const uint8_t tn = st_[eo + EY(a) * SH::EXT_X + EX(a)];
           if (is_fluid(tn))
             st<TF, R>(fo + a * N + nb[a], fs);
           else if (!is_res(tn))
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
             int dst = node, slot = a;            // rest population stays
             bool keep = true;
             if (a > 0) {
-              const int en = eo + EY(a) * EXT_X + EX(a);
+              const int en = eo + EY(a) * SH::EXT_X + EX(a);
               const uint8_t tn = st_[en];
               const bool mn = sm_[en] != 0;
               if (is_fluid(tn) && mn) {
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
         }
       }
     } else if (own) {
-      if (is_res(t)) reservoir_push<R, TF, TG, NS>(P, tin, fin, gin, fout, gout, N, x, y, t, step, theta, st_, sm_, eo);
+      if (is_res(t)) reservoir_push<SH, R, TF, TG, NS>(P, tin, fin, gin, fout, gout, N, x, y, t, step, theta, st_, sm_, eo);
       tout[node] = t;
     }
 

@@ -15,21 +15,24 @@ constexpr uint8_t T_MASK = 0x0F;     // low nibble: node type
 constexpr uint8_t T_NEW = 0x40;      // flag set by the amendment kernel: solid -> liquid this step
 constexpr uint8_t T_VANISH = 0x80;   // flag: liquid -> solid this step
 
-// Tile shape of the bulk kernels (one thread per interior node); 16x16 measured
-// fastest of 32x8, 64x4, 32x16, 16x16 and 64x8 on the porous workload.
-#ifndef PSLBM_TX
-#define PSLBM_TX 16
-#endif
-#ifndef PSLBM_TY
-#define PSLBM_TY 16
-#endif
-constexpr int TX = PSLBM_TX;
-constexpr int TY = PSLBM_TY;
-constexpr int EXT_X = TX + 2;
-constexpr int EXT_Y = TY + 2;
-constexpr int EXT = EXT_X * EXT_Y;
-constexpr int RING = EXT - TX * TY;
-constexpr int NTHREADS = TX * TY;
+// Tile shapes of the step kernels: 256 threads, one per interior node, and a
+// one-node ring.  The runtime picks the faster shape per handle or batch by
+// timing its first steps (results do not depend on the shape).
+constexpr int NTHREADS = 256;
+template <int TX_, int TY_>
+struct TileShape {
+  static constexpr int TX = TX_, TY = TY_;
+  static constexpr int EXT_X = TX + 2, EXT_Y = TY + 2;
+  static constexpr int EXT = EXT_X * EXT_Y;
+  static constexpr int RING = EXT - TX * TY;
+  static_assert(TX * TY == NTHREADS, "one thread per interior node");
+  static_assert(RING <= NTHREADS, "one ring node per thread");
+};
+using ShapeA = TileShape<16, 16>;
+using ShapeB = TileShape<32, 8>;
+constexpr int NSHAPES = 2;
+constexpr int SHAPE_TX[NSHAPES] = {ShapeA::TX, ShapeB::TX};
+constexpr int SHAPE_TY[NSHAPES] = {ShapeA::TY, ShapeB::TY};
 
 // Per-instance scalar slots (unsigned long long each).
 enum {
@@ -102,7 +105,6 @@ struct DevInst {
   unsigned long long* scal;   // [S_NSCAL]
   long long N;
   int evcap;
-  int ntiles;
 };
 
 struct Tile {

@@ -20,11 +20,11 @@ namespace pslbm {
 // D(s) or F(s)); E gains the B consumed on the same link.  Then V_D -= Vbar_D
 // sum q_B, V_F += Vbar_F sum q_F, and the node dissolves, overflows or changes
 // between D(s) and F(s).
-template <class TF, class TG, class R, int NS>
+template <class SH, class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles, int ntiles,
                                                    const DevInst* __restrict__ insts) {
   const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
+  const int tx = tid % SH::TX, ty = tid / SH::TX;
   for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
     const Tile tl = tiles[ti];
     const DevInst* Ip = insts + tl.inst;

@@ -11,27 +11,27 @@ namespace {
 
 // Persistent grid: as many blocks as fit on the device at once (capped by the
 // tile count); each block walks the tile list with a stride of the grid size.
-template <int NS>
+template <class SH, int NS>
 int bulk_grid(int ntiles) {
   static int cap = 0;
   if (cap == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk<KTF, KTG, KR, NS>, NTHREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk<SH, KTF, KTG, KR, NS>, NTHREADS, 0);
     cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
   return ntiles < cap ? ntiles : cap;
 }
-template <int NS>
+template <class SH, int NS>
 void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
   if (ntiles <= 0) return;
-  k_bulk<KTF, KTG, KR, NS><<<bulk_grid<NS>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
+  k_bulk<SH, KTF, KTG, KR, NS><<<bulk_grid<SH, NS>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
 }
-template <int NS>
+template <class SH, int NS>
 void vop_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
   if (ntiles <= 0) return;
-  k_vop<KTF, KTG, KR, NS><<<ntiles, NTHREADS, 0, s>>>(tiles, ntiles, insts);
+  k_vop<SH, KTF, KTG, KR, NS><<<ntiles, NTHREADS, 0, s>>>(tiles, ntiles, insts);
 }
 template <int NS>
 void amend_l(cudaStream_t s, int ninst, const DevInst* insts) {
@@ -60,7 +60,7 @@ void budget_l(cudaStream_t s, const DevInst* I, double* part, double* out) {
 
 template <int NS>
 constexpr Launchers make() {
-  return Launchers{&bulk_l<NS>, &vop_l<NS>, &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
+  return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>}, {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>}, &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
 }
 const Launchers table[MAXS + 1] = {make<0>(), make<1>(), make<2>(), make<3>(), make<4>()};
 

@@ -6,8 +6,8 @@
 namespace pslbm {
 
 struct Launchers {
-  void (*bulk)(cudaStream_t, const Tile*, int ntiles, const DevInst*);
-  void (*vop)(cudaStream_t, const Tile*, int ntiles, const DevInst*);
+  void (*bulk[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
+  void (*vop[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
   void (*amend)(cudaStream_t, int ninst, const DevInst*);
   void (*init)(cudaStream_t, DevInst*, const uint8_t*, const double*, const double*, const double*, long long N);
   void (*fields)(cudaStream_t, const DevInst*, long long N, double*, double*, double*, double*, double*, uint8_t*);

@@ -42,6 +42,29 @@ struct GraphCache {
   }
 };
 
+// Launch state shared by a single simulation and a batch: one tile list per
+// tile shape (built on demand), the chosen shape, and the captured graphs.
+struct Stepper {
+  const Launchers* L = nullptr;
+  DevInst* d = nullptr;
+  int ninst = 0;
+  std::vector<std::pair<int, int>> dims;   // (nx, ny) per instance
+  Tile* tiles[NSHAPES] = {};
+  int ntiles[NSHAPES] = {};
+  int shape = 0;
+  bool tuned = false;                      // shape chosen (by timing or by the caller)
+  GraphCache graphs;
+  double trial_ms[NSHAPES] = {};
+  void release() {
+    graphs.clear();
+    for (int s = 0; s < NSHAPES; ++s) {
+      if (tiles[s]) cudaFree(tiles[s]);
+      tiles[s] = nullptr;
+      ntiles[s] = 0;
+    }
+  }
+};
+
 }  // namespace
 
 struct pslbm_s {
@@ -51,15 +74,13 @@ struct pslbm_s {
   long long N = 0;
   DevInst h{};                 // host copy of the device descriptor
   DevInst* d = nullptr;        // device descriptor
-  Tile* tiles = nullptr;
-  int ntiles = 0;
+  Stepper run;
   std::vector<void*> allocs;
   uint64_t bytes = 0;
   double* rb = nullptr;        // read-back scratch
   size_t rb_bytes = 0;
   std::string err;
   pslbm_status sticky = PSLBM_OK;
-  GraphCache graphs;
   int in_batch = 0;
   const Launchers* L = nullptr;
 };
@@ -67,9 +88,7 @@ struct pslbm_s {
 struct pslbm_batch_s {
   std::vector<pslbm_t> members;
   DevInst* d = nullptr;
-  Tile* tiles = nullptr;
-  int ntiles = 0;
-  GraphCache graphs;
+  Stepper run;
   const Launchers* L = nullptr;
   std::string err;
   pslbm_status sticky = PSLBM_OK;
@@ -263,11 +282,33 @@ DevParams to_dev(const pslbm_params* p) {
   return P;
 }
 
-std::vector<Tile> make_tiles(int inst, int nx, int ny) {
+std::vector<Tile> make_tiles(int inst, int nx, int ny, int shape) {
   std::vector<Tile> t;
-  for (int y0 = 0; y0 < ny; y0 += TY)
-    for (int x0 = 0; x0 < nx; x0 += TX) t.push_back(Tile{inst, x0, y0, 0});
+  for (int y0 = 0; y0 < ny; y0 += SHAPE_TY[shape])
+    for (int x0 = 0; x0 < nx; x0 += SHAPE_TX[shape]) t.push_back(Tile{inst, x0, y0, 0});
   return t;
+}
+
+// Tile list of every instance of a stepper for one shape (device copy).
+cudaError_t ensure_tiles(Stepper& st, int shape) {
+  if (st.tiles[shape]) return cudaSuccess;
+  std::vector<Tile> all;
+  for (int i = 0; i < (int)st.dims.size(); ++i) {
+    std::vector<Tile> t = make_tiles(i, st.dims[i].first, st.dims[i].second, shape);
+    all.insert(all.end(), t.begin(), t.end());
+  }
+  Tile* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, all.size() * sizeof(Tile));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice, lib_stream());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(lib_stream());
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return e;
+  }
+  st.tiles[shape] = d;
+  st.ntiles[shape] = (int)all.size();
+  return cudaSuccess;
 }
 
 pslbm_status dalloc(pslbm_t h, void** ptr, size_t bytes) {
@@ -286,25 +327,75 @@ pslbm_status dalloc(pslbm_t h, void** ptr, size_t bytes) {
 }
 
 void free_all(pslbm_t h) {
-  h->graphs.clear();
+  h->run.release();
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
 }
 
-// Enqueue n steps of the kernels over a tile list.
-void enqueue_steps(cudaStream_t s, const Launchers* L, const Tile* tiles, int ntiles, const DevInst* d, int ninst,
-                   int64_t n) {
+// Enqueue n steps of the kernels over the tile list of one shape.
+void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int64_t n) {
   for (int64_t i = 0; i < n; ++i) {
-    L->bulk(s, tiles, ntiles, d);
-    L->vop(s, tiles, ntiles, d);
-    L->amend(s, ninst, d);
+    st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
+    st.L->vop[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
+    st.L->amend(s, st.ninst, st.d);
   }
 }
 
-// Run n steps, replaying captured graphs of up to 32 steps.
-pslbm_status run_steps(GraphCache& gc, const Launchers* L, const Tile* tiles, int ntiles, const DevInst* d,
-                       int ninst, int64_t n, std::string& err) {
+// Tile-shape autotuning: the results do not depend on the shape (the per-node
+// arithmetic and the fixed-order gathers are the same), so the first steps of a
+// run are spent timing each shape (one untimed step, then TUNE_STEPS timed
+// steps per shape) and the fastest is kept.
+constexpr int TUNE_STEPS = 3;
+pslbm_status autotune(Stepper& st, std::string& err) {
   cudaStream_t s = lib_stream();
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    err = "cudaEventCreate failed";
+    return PSLBM_ERR_CUDA;
+  }
+  int best = 0;
+  for (int sh = 0; sh < NSHAPES; ++sh) {
+    cudaError_t e = ensure_tiles(st, sh);
+    if (e != cudaSuccess) {
+      err = std::string("tile list: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA;
+    }
+    enqueue_steps(s, st, sh, 1);
+    cudaEventRecord(a, s);
+    enqueue_steps(s, st, sh, TUNE_STEPS);
+    cudaEventRecord(b, s);
+    e = cudaEventSynchronize(b);
+    if (e != cudaSuccess) {
+      err = std::string("autotune: ") + cudaGetErrorString(e);
+      return PSLBM_ERR_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    st.trial_ms[sh] = ms / TUNE_STEPS;
+    if (st.trial_ms[sh] < st.trial_ms[best]) best = sh;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (best != st.shape) st.graphs.clear();
+  st.shape = best;
+  st.tuned = true;
+  return PSLBM_OK;
+}
+
+// Run n steps, replaying captured graphs of up to 32 steps.
+pslbm_status run_steps(Stepper& st, int64_t n, std::string& err) {
+  cudaStream_t s = lib_stream();
+  if (!st.tuned && n >= NSHAPES * (TUNE_STEPS + 1) + 1) {
+    pslbm_status ts = autotune(st, err);
+    if (ts != PSLBM_OK) return ts;
+    n -= NSHAPES * (TUNE_STEPS + 1);
+  }
+  cudaError_t te = ensure_tiles(st, st.shape);
+  if (te != cudaSuccess) {
+    err = std::string("tile list: ") + cudaGetErrorString(te);
+    return PSLBM_ERR_CUDA;
+  }
+  GraphCache& gc = st.graphs;
   const int64_t K = 32;
   while (n > 0) {
     const int64_t k = n >= K ? K : n;
@@ -316,7 +407,7 @@ pslbm_status run_steps(GraphCache& gc, const Launchers* L, const Tile* tiles, in
         err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
         return PSLBM_ERR_CUDA;
       }
-      enqueue_steps(s, L, tiles, ntiles, d, ninst, k);
+      enqueue_steps(s, st, st.shape, k);
       e = cudaStreamEndCapture(s, &g);
       if (e != cudaSuccess) {
         err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
@@ -339,6 +430,22 @@ pslbm_status run_steps(GraphCache& gc, const Launchers* L, const Tile* tiles, in
     n -= k;
   }
   return PSLBM_OK;
+}
+
+// Fix the tile shape (tx = ty = 0: choose by timing on the next long run).
+pslbm_status set_shape(Stepper& st, int tx, int ty) {
+  if (tx == 0 && ty == 0) {
+    st.tuned = false;
+    return PSLBM_OK;
+  }
+  for (int sh = 0; sh < NSHAPES; ++sh)
+    if (SHAPE_TX[sh] == tx && SHAPE_TY[sh] == ty) {
+      if (sh != st.shape) st.graphs.clear();
+      st.shape = sh;
+      st.tuned = true;
+      return PSLBM_OK;
+    }
+  return PSLBM_ERR_PARAM;
 }
 
 pslbm_status device_status(pslbm_t h) {
@@ -387,9 +494,6 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   I.P = to_dev(p);
   I.N = N;
   I.evcap = (int)N;
-  std::vector<Tile> tl = make_tiles(0, p->nx, p->ny);
-  I.ntiles = (int)tl.size();
-  h->ntiles = I.ntiles;
   pslbm_status st = PSLBM_OK;
   void* ptr;
 #define AL(field, bytes)                                     \
@@ -410,7 +514,6 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   AL(I.claim, (size_t)N * sizeof(int));
   AL(I.scal, S_NSCAL * sizeof(unsigned long long));
   AL(h->d, sizeof(DevInst));
-  AL(h->tiles, tl.size() * sizeof(Tile));
   {
     // staging copies of the inputs
     uint8_t* dmask = nullptr;
@@ -451,7 +554,6 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
       }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d, &I, sizeof(DevInst), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
       L->init(s, h->d, dmask, dr1, dr2, dc, N);
       e = cudaGetLastError();
@@ -495,6 +597,18 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
     }
   }
 #undef AL
+  h->run.L = L;
+  h->run.d = h->d;
+  h->run.ninst = 1;
+  h->run.dims.assign(1, {p->nx, p->ny});
+  {
+    cudaError_t e = ensure_tiles(h->run, h->run.shape);
+    if (e != cudaSuccess) {
+      st = fail(nullptr, e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA,
+                std::string("tile list: ") + cudaGetErrorString(e));
+      goto fail_cleanup;
+    }
+  }
   *out = h;
   return PSLBM_OK;
 fail_cleanup : {
@@ -516,7 +630,7 @@ pslbm_status pslbm_step(pslbm_t h, int64_t n) {
   if (h->in_batch) return fail(h, PSLBM_ERR_STATE, "handle is a member of a batch; step the batch");
   if (n == 0) return PSLBM_OK;
   std::string err;
-  pslbm_status st = run_steps(h->graphs, h->L, h->tiles, h->ntiles, h->d, 1, n, err);
+  pslbm_status st = run_steps(h->run, n, err);
   if (st != PSLBM_OK) return fail(h, st, err);
   return PSLBM_OK;
 }
@@ -532,10 +646,11 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
   double acc[3] = {0, 0, 0}, tot = 0;
   pslbm_status st = PSLBM_OK;
   for (int64_t i = 0; i < n && st == PSLBM_OK; ++i) {
+    const int sh = h->run.shape;
     cudaEventRecord(ev[0], s);
-    h->L->bulk(s, h->tiles, h->ntiles, h->d);
+    h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[1], s);
-    h->L->vop(s, h->tiles, h->ntiles, h->d);
+    h->L->vop[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[2], s);
     h->L->amend(s, 1, h->d);
     cudaEventRecord(ev[3], s);
@@ -575,8 +690,25 @@ pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes)
   const uint64_t N = (uint64_t)p->nx * (uint64_t)p->ny;
   const uint64_t per = 2 * 18 * fsize(p->precision) + 2 * 5 * (uint64_t)p->n_species * gsize(p->precision) +
                        2 /*types*/ + 16 /*V*/ + 1 /*events*/ + 8 /*excess*/ + 8 /*event lists*/ + 4 /*claims*/;
-  const uint64_t tiles = ((uint64_t)(p->nx + TX - 1) / TX) * ((uint64_t)(p->ny + TY - 1) / TY);
+  uint64_t tiles = 0;
+  for (int sh = 0; sh < NSHAPES; ++sh)
+    tiles += ((uint64_t)(p->nx + SHAPE_TX[sh] - 1) / SHAPE_TX[sh]) * ((uint64_t)(p->ny + SHAPE_TY[sh] - 1) / SHAPE_TY[sh]);
   *bytes = N * per + tiles * sizeof(Tile) + sizeof(DevInst) + S_NSCAL * 8 + 12 * 16;
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_set_tile_shape(pslbm_t h, int32_t tile_x, int32_t tile_y) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (set_shape(h->run, tile_x, tile_y) != PSLBM_OK)
+    return fail(h, PSLBM_ERR_PARAM, "unsupported tile shape (0x0, 16x16 or 32x8)");
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, int32_t* tuned) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (tile_x) *tile_x = SHAPE_TX[h->run.shape];
+  if (tile_y) *tile_y = SHAPE_TY[h->run.shape];
+  if (tuned) *tuned = h->run.tuned ? 1 : 0;
   return PSLBM_OK;
 }
 
@@ -702,8 +834,6 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
   if (!out) return fail(nullptr, PSLBM_ERR_PARAM, "out is NULL");
   *out = nullptr;
   if (n < 1 || !members) return fail(nullptr, PSLBM_ERR_PARAM, "empty batch");
-  if (!((tile_x == 0 || tile_x == TX) && (tile_y == 0 || tile_y == TY)))
-    return fail(nullptr, PSLBM_ERR_PARAM, "unsupported tile shape");
   for (int i = 0; i < n; ++i) {
     if (!members[i] || members[i]->sticky) return fail(nullptr, PSLBM_ERR_PARAM, "invalid member");
     if (members[i]->in_batch) return fail(nullptr, PSLBM_ERR_STATE, "member already in a batch");
@@ -714,29 +844,32 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
   }
   pslbm_batch_t b = new (std::nothrow) pslbm_batch_s();
   if (!b) return fail(nullptr, PSLBM_ERR_OOM, "host allocation failed");
+  if (set_shape(b->run, tile_x, tile_y) != PSLBM_OK) {
+    delete b;
+    return fail(nullptr, PSLBM_ERR_PARAM, "unsupported tile shape (0x0, 16x16 or 32x8)");
+  }
   std::vector<DevInst> di;
-  std::vector<Tile> tl;
   for (int i = 0; i < n; ++i) {
     b->members.push_back(members[i]);
     di.push_back(members[i]->h);
-    std::vector<Tile> t = make_tiles(i, members[i]->p.nx, members[i]->p.ny);
-    tl.insert(tl.end(), t.begin(), t.end());
+    b->run.dims.push_back({members[i]->p.nx, members[i]->p.ny});
   }
   cudaStream_t s = lib_stream();
   cudaError_t e = cudaMalloc(&b->d, di.size() * sizeof(DevInst));
-  if (e == cudaSuccess) e = cudaMalloc(&b->tiles, tl.size() * sizeof(Tile));
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d, di.data(), di.size() * sizeof(DevInst), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->tiles, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  b->L = members[0]->L;
+  b->run.L = b->L;
+  b->run.d = b->d;
+  b->run.ninst = n;
+  if (e == cudaSuccess) e = ensure_tiles(b->run, b->run.shape);
   if (e != cudaSuccess) {
+    b->run.release();
     if (b->d) cudaFree(b->d);
-    if (b->tiles) cudaFree(b->tiles);
     delete b;
     return fail(nullptr, e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA,
                 std::string("batch create: ") + cudaGetErrorString(e));
   }
-  b->ntiles = (int)tl.size();
-  b->L = members[0]->L;
   for (int i = 0; i < n; ++i) members[i]->in_batch = 1;
   *out = b;
   return PSLBM_OK;
@@ -748,12 +881,20 @@ pslbm_status pslbm_batch_step(pslbm_batch_t b, int64_t n) {
   if (n < 0) return fail(nullptr, PSLBM_ERR_PARAM, "n < 0");
   if (n == 0) return PSLBM_OK;
   std::string err;
-  pslbm_status st = run_steps(b->graphs, b->L, b->tiles, b->ntiles, b->d, (int)b->members.size(), n, err);
+  pslbm_status st = run_steps(b->run, n, err);
   if (st != PSLBM_OK) {
     b->sticky = st;
     b->err = err;
     return fail(nullptr, st, err);
   }
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_batch_get_tile_shape(pslbm_batch_t b, int32_t* tile_x, int32_t* tile_y, int32_t* tuned) {
+  if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
+  if (tile_x) *tile_x = SHAPE_TX[b->run.shape];
+  if (tile_y) *tile_y = SHAPE_TY[b->run.shape];
+  if (tuned) *tuned = b->run.tuned ? 1 : 0;
   return PSLBM_OK;
 }
 
@@ -772,9 +913,8 @@ pslbm_status pslbm_batch_sync(pslbm_batch_t b) {
 pslbm_status pslbm_batch_destroy(pslbm_batch_t b) {
   if (!b) return PSLBM_OK;
   cudaStreamSynchronize(lib_stream());
-  b->graphs.clear();
+  b->run.release();
   if (b->d) cudaFree(b->d);
-  if (b->tiles) cudaFree(b->tiles);
   for (pslbm_t m : b->members) m->in_batch = 0;
   delete b;
   return PSLBM_OK;

@@ -28,7 +28,8 @@ EXPORTS = ["pslbm_get_stream", "pslbm_set_stream", "pslbm_create", "pslbm_step",
            "pslbm_batch_create", "pslbm_batch_step", "pslbm_batch_sync", "pslbm_batch_destroy",
            "pslbm_budget_device_noalloc", "pslbm_set_step_limit", "pslbm_estimate_device_bytes",
            "pslbm_server_create", "pslbm_server_submit", "pslbm_server_advance", "pslbm_server_poll",
-           "pslbm_server_fetch", "pslbm_server_release", "pslbm_server_last_error", "pslbm_server_destroy"]
+           "pslbm_server_fetch", "pslbm_server_release", "pslbm_server_last_error", "pslbm_server_destroy",
+           "pslbm_set_tile_shape", "pslbm_get_tile_shape", "pslbm_batch_get_tile_shape"]
 
 _D2 = C.c_double * 2
 _DS = C.c_double * MAX_SPECIES
@@ -133,6 +134,9 @@ def load():
     lib.pslbm_server_last_error.argtypes = [vp]
     lib.pslbm_server_last_error.restype = C.c_char_p
     lib.pslbm_server_destroy.argtypes = [vp]
+    lib.pslbm_set_tile_shape.argtypes = [vp, i32, i32]
+    lib.pslbm_get_tile_shape.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    lib.pslbm_batch_get_tile_shape.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("pslbm_get_stream", "pslbm_last_error", "pslbm_server_last_error"):
@@ -195,6 +199,14 @@ class Simulation:
         t = C.c_double()
         _check(load().pslbm_profile_step(self.h, int(n), k, C.byref(t)), self.h)
         return dict(bulk=k[0], vop=k[1], amend=k[2]), t.value
+
+    def set_tile_shape(self, tx, ty):
+        _check(load().pslbm_set_tile_shape(self.h, int(tx), int(ty)), self.h)
+
+    def tile_shape(self):
+        tx, ty, tu = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().pslbm_get_tile_shape(self.h, C.byref(tx), C.byref(ty), C.byref(tu)), self.h)
+        return tx.value, ty.value, bool(tu.value)
 
     def set_step_limit(self, limit):
         _check(load().pslbm_set_step_limit(self.h, int(limit)), self.h)
@@ -274,6 +286,11 @@ class Batch:
 
     def sync(self):
         _check(load().pslbm_batch_sync(self.b))
+
+    def tile_shape(self):
+        tx, ty, tu = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().pslbm_batch_get_tile_shape(self.b, C.byref(tx), C.byref(ty), C.byref(tu)))
+        return tx.value, ty.value, bool(tu.value)
 
     def close(self):
         if getattr(self, "b", None):

@@ -239,3 +239,25 @@ def test_step_counts_and_graph_replay(pslbm):
         r2 = s2.read()
     for k in ("rho1", "ux", "conc", "type", "vol"):
         assert np.array_equal(r1[k], r2[k]), k
+
+
+def test_tile_shapes_and_autotune_agree(pslbm):
+    """The step kernels exist for 16x16 and 32x8 tiles; a run pinned to either
+    shape and an autotuned run (which times both on its first 8 steps) give
+    bit-identical fields, and the autotuned handle reports its choice."""
+    sc = inputs.porous_discs(nx=150, ny=90, seed=21, slug=(12, 6))
+    res = []
+    for shape in ((16, 16), (32, 8), (0, 0)):
+        with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"]) as s:
+            s.set_tile_shape(*shape)
+            s.step(40)
+            tx, ty, tuned = s.tile_shape()
+            assert tuned
+            if shape != (0, 0):
+                assert (tx, ty) == shape
+            else:
+                assert (tx, ty) in ((16, 16), (32, 8))
+            res.append(s.read())
+    for r in res[1:]:
+        for k in ("rho1", "rho2", "ux", "uy", "conc", "type", "vol"):
+            assert np.array_equal(r[k], res[0][k]), k
