@@ -2,9 +2,10 @@
 """Throughput benchmark of the reactive two-phase LBM step on GB300.
 
 Workload: the porous-medium reactive two-phase lattice (1024x512, seeded
-overlapping D(s) discs of radius 8-24 at porosity 0.6, inlet reservoir with
-liquid and gas slugs, outlet reservoir, species B, E, F transported and A
-derived, R1-R4), FP32 compute with shifted FP32 storage.  One step is one pass
+overlapping D(s) discs of radius 8-24 at porosity 0.6, liquid inflow from an
+inlet reservoir, phase-following outlet reservoir, seeded gas slugs in the
+pores, species B, E, F transported and A derived, R1-R4), FP32 compute with
+shifted FP32 storage.  One step is one pass
 of the whole hot path: the fused bulk kernel, the VOP kernel and the
 amendment kernel.
 
@@ -35,7 +36,8 @@ import numpy as np  # noqa: E402
 
 WORKLOAD = dict(nx=1024, ny=512, seed=1)
 SAMPLE = dict(nx=256, ny=128, seed=1)
-WORKLOAD_NAME = ("porous discs 1024x512 (radii 8-24, porosity 0.6, seed 1), inlet liquid/gas slugs + outlet, "
+WORKLOAD_NAME = ("porous discs 1024x512 (radii 8-24, porosity 0.6, seed 1), pressure-driven liquid inflow "
+                 "(inlet 1% over coexistence, phase-following outlet), seeded gas slugs in the pores, "
                  "species B,E,F transported + A derived, R1-R4 (k1=1e-5, k3=1e-1, k2=1e-3, k4=1e-3)")
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_bulk_porous1024x512_fp32.json")
 
