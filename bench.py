@@ -148,15 +148,9 @@ def sample_desc(n, el):
 
 # ------------------------------------------------------------------ arms
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def reference_arm(args):
-    ws, rank, _ = dist_env()
+    from paper_1410_3464_gb300 import replicas
+    ws, rank, _ = replicas.env()
     if rank != 0:
         return 0
     mlups_w, _, _ = oracle_run(0, max_steps=max(1, args.warmup), warmup=0)
@@ -174,13 +168,11 @@ def reference_arm(args):
 
 def ours_arm(args):
     import torch
-    import torch.distributed as dist
 
-    from paper_1410_3464_gb300 import inputs, pslbm
+    from paper_1410_3464_gb300 import inputs, pslbm, replicas
 
-    ws, rank, local = dist_env()
-    if ws > 1:
-        dist.init_process_group("gloo", init_method="env://")
+    ws, rank, local = replicas.env()
+    replicas.init(ws)
     torch.cuda.set_device(local)
     prec = {"fp32": pslbm.FP32, "fp64": pslbm.FP64, "fp32_f16": pslbm.FP32_SOLUTE_F16,
             "fp32_bf16": pslbm.FP32_SOLUTE_BF16}[args.precision]
@@ -203,8 +195,7 @@ def ours_arm(args):
     n_fluid = int((t <= 1).sum())
     n_liq = int((t == 0).sum())
 
-    if ws > 1:
-        dist.barrier()
+    replicas.barrier(ws)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -221,13 +212,9 @@ def ours_arm(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     sim.sync()
-    my_ms = float(sum(tot))
-    if ws > 1:
-        tt = torch.tensor([my_ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        my_ms = float(tt.item())
-    total_nodes = N * args.steps * ws
-    value = total_nodes / (my_ms * 1e-3) / 1e6
+    replicas.barrier(ws)
+    my_ms = replicas.max_over_ranks(float(sum(tot)), ws)
+    value = replicas.whole_job_rate(N * args.steps, ws, my_ms * 1e-3) / 1e6
     bulk_ms = statistics.mean(kern["bulk"])
     bytes_per_launch = n_fluid * 36 * fs + n_liq * 10 * ns * gs + 2 * N
     peaks = {}
@@ -264,35 +251,36 @@ def ours_arm(args):
         line["clocks"] = clk
 
     if not args.skip_cpu:
-        # end to end through the C ABI with host buffers: create (H2D of the
-        # initial state), K steps, read of all fields (D2H)
+        # end to end through the C ABI with host buffers: create (host->device
+        # copy of the scene), then every step a step call and a read of that
+        # step's budget to the host, then a read of all fields
+        replicas.barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim2 = pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
                                 precision=prec)
-        sim2.step(args.steps)
+        bud_bytes = 0
+        for _ in range(args.steps):
+            sim2.step(1)
+            bud = sim2.read(pslbm.F_BUDGET)["budget"]
+            bud_bytes += bud.nbytes
         out = sim2.read(pslbm.F_RHO1 | pslbm.F_RHO2 | pslbm.F_UX | pslbm.F_UY | pslbm.F_CONC | pslbm.F_TYPE |
                         pslbm.F_VOL)
         el = time.perf_counter() - t0
         sim2.close()
         h2d = sc["mask"].nbytes + sc["rho1"].nbytes + sc["rho2"].nbytes + sc["conc"].nbytes
-        d2h = sum(v.nbytes for k, v in out.items() if k not in ("vol_d", "vol_f"))
-        e2e_val = N * args.steps / el / 1e6
-        if ws > 1:
-            tt = torch.tensor([el], dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_val = N * args.steps * ws / float(tt.item()) / 1e6
+        d2h = sum(v.nbytes for v in out.values()) + bud_bytes
+        e2e_val = replicas.whole_job_rate(N * args.steps, ws, replicas.max_over_ranks(el, ws)) / 1e6
         line["e2e"] = {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                        "d2h_bytes_per_step": d2h / args.steps,
-                       "note": "initial state copied at create, all fields read back after the last step"}
+                       "note": "scene copied at create; each step's budget read to the host; all fields read "
+                               "after the last step"}
         if rank == 0:
             mlups, n, elc = oracle_run(10.0)
             line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                                     "sample": sample_desc(n, elc)}
     sim.close()
-    if ws > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+    replicas.finish(ws)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
