@@ -55,7 +55,7 @@ typedef enum {
 
 typedef enum {
     PSLBM_FP64 = 0,              /* populations stored and computed in FP64 */
-    PSLBM_FP32 = 1,              /* FP32 compute, populations stored as f - w_a rho_ref (shifted) */
+    PSLBM_FP32 = 1,              /* FP32 compute, populations stored as f - w_a rho_ref(phase) (shifted) */
     PSLBM_FP32_SOLUTE_F16 = 2,   /* as FP32, solute populations stored in IEEE half */
     PSLBM_FP32_SOLUTE_BF16 = 3   /* as FP32, solute populations stored in bfloat16 */
 } pslbm_precision;
@@ -84,8 +84,9 @@ typedef struct {
     double w_adh[2];               /* Eq. 16 fluid-solid interaction strengths */
     double eos_a, eos_b, eos_R, eos_T; /* Eq. 12 Carnahan-Starling constants and temperature */
     double body_force[2];          /* optional uniform acceleration (x, y) */
-    double rho_ref[2];             /* reference densities: FP32 population shift and the
-                                      fill density of a refilled node with no fluid neighbour */
+    double rho_ref[2];             /* reference densities of the liquid phase: FP32 population
+                                      shift of liquid-marked nodes and the fill density of a
+                                      refilled node with no fluid neighbour */
     /* solutes: Eqs. 20-24 */
     int32_t n_species;             /* transported species, 0..PSLBM_MAX_SPECIES */
     int32_t idx_A, idx_B, idx_E, idx_F; /* species index of A, B, E, F; -1 absent; A may be -2 (derived) */
@@ -110,6 +111,10 @@ typedef struct {
     int32_t inlet_ramp;            /* steps of linear blend between the liquid and gas inlet
                                       states at the end of each slug (0: sharp switch) */
     double conc_in[PSLBM_MAX_SPECIES];  /* inlet concentrations */
+    double rho_ref_gas[2];         /* reference densities of the gas phase: FP32 population
+                                      shift of gas-marked nodes (each node's populations are
+                                      stored relative to its own phase, so that both phases
+                                      keep their FP32 digits at a large density ratio) */
 } pslbm_params;
 
 /* Field selectors for pslbm_read_fields; each selected field has its own
@@ -177,11 +182,25 @@ pslbm_status pslbm_set_step_limit(pslbm_t h, int64_t limit);
 pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes);
 
 /* Tile shape of the step kernels: 16x16 or 32x8 nodes per 256-thread block.
- * (0, 0), the default, lets the next step call of at least 9 steps time both
- * shapes on its first 8 steps and keep the faster; the results do not depend on
- * the shape.  tuned reports whether a shape has been chosen. */
+ * (0, 0), the default, leaves the shape to timing: the next step call long
+ * enough to try every open variant (tile shape x staging, 4 steps each, which
+ * advance the simulation like any others) times them and keeps the fastest;
+ * the results do not depend on the variant.  tuned reports whether the variant
+ * has been chosen (by timing, or because only one was left open). */
 pslbm_status pslbm_set_tile_shape(pslbm_t h, int32_t tile_x, int32_t tile_y);
 pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, int32_t* tuned);
+
+/* Staging of the bulk kernel's populations: 0 plain per-thread loads, 1 TMA
+ * copies of each tile's population box into shared memory two tiles ahead
+ * (available for the FP32-population precisions when a row of the lattice is a
+ * multiple of 16 bytes: nx a multiple of 4, and of 8 with 16-bit solutes),
+ * -1 (the default) leaves it to timing.  PSLBM_ERR_PARAM for 1 where it is not
+ * available.  The results are bit-identical either way.  get reports the
+ * staging in use and whether staging is available for the handle.  A staged
+ * kernel whose copy does not arrive within about a second stops and sets
+ * PSLBM_ERR_TIMEOUT (sticky), reported by the next sync or read. */
+pslbm_status pslbm_set_staging(pslbm_t h, int32_t mode);
+pslbm_status pslbm_get_staging(pslbm_t h, int32_t* staged, int32_t* available);
 
 /* Number of steps taken and lattice size. */
 pslbm_status pslbm_info(pslbm_t h, int64_t* steps, int32_t* nx, int32_t* ny, int32_t* n_species);
@@ -226,6 +245,10 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
 pslbm_status pslbm_batch_step(pslbm_batch_t b, int64_t n);
 pslbm_status pslbm_batch_sync(pslbm_batch_t b);
 pslbm_status pslbm_batch_get_tile_shape(pslbm_batch_t b, int32_t* tile_x, int32_t* tile_y, int32_t* tuned);
+/* Staging for the batch as for a single handle; available only when every
+ * member has it. */
+pslbm_status pslbm_batch_set_staging(pslbm_batch_t b, int32_t mode);
+pslbm_status pslbm_batch_get_staging(pslbm_batch_t b, int32_t* staged, int32_t* available);
 pslbm_status pslbm_batch_destroy(pslbm_batch_t b);
 
 /* ---------------------------------------------------------------- serving

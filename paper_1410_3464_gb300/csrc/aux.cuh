@@ -22,8 +22,8 @@ __global__ void k_init(DevInst* __restrict__ Ip, const uint8_t* __restrict__ mas
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const R w = w9<R>(a);
-      st<TF, R>(F + a * N + node, fl ? w * r1 - w * rp<R>(P).shift_f[0] : R(0));
-      st<TF, R>(F + (9 + a) * N + node, fl ? w * r2 - w * rp<R>(P).shift_f[1] : R(0));
+      st<TF, R>(F + a * N + node, fl ? w * r1 - w * fshift<R>(P, 0, t) : R(0));
+      st<TF, R>(F + (9 + a) * N + node, fl ? w * r2 - w * fshift<R>(P, 1, t) : R(0));
     }
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
@@ -69,7 +69,7 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
       R d1 = f1[0], d2 = f2[0];
 #pragma unroll
       for (int a = 1; a < 9; ++a) { d1 += f1[a]; d2 += f2[a]; }
-      const R rho1 = rp<R>(P).shift_f[0] + d1, rho2 = rp<R>(P).shift_f[1] + d2;
+      const R rho1 = fshift<R>(P, 0, t) + d1, rho2 = fshift<R>(P, 1, t) + d2;
       const R j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
       const R j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
       const R j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
@@ -87,11 +87,11 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
         if (is_live(tn)) {
           R a1, a2;
           if (is_fluid(tn)) {
-            a1 = rp<R>(P).shift_f[0] + density_shifted<R>(F, N, nn);
-            a2 = rp<R>(P).shift_f[1] + density_shifted<R>(F + 9 * N, N, nn);
+            a1 = fshift<R>(P, 0, tn) + density_shifted<R>(F, N, nn);
+            a2 = fshift<R>(P, 1, tn) + density_shifted<R>(F + 9 * N, N, nn);
           } else {
             double u, v;
-            const R theta = R(0.5 * ord_dec(Ip->scal[S_MAX0 + cur]));
+            const R theta = theta_of<R>(Ip);
             reservoir_rho(P, tn, step, tn == T_OUTLET && outlet_up_liquid<R, TF>(P, T, F, (int)N, (int)nn, theta), u, v);
             a1 = R(u);
             a2 = R(v);
@@ -100,7 +100,8 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
           sv = R(0);
         }
         const R w = wf<R>(a);
-        const R vp = w * ps, v2 = w * q2, v1 = w * q1, vs = w * sv;
+        // differences from the centre value, as in the bulk kernel
+        const R vp = w * (ps - psc), v2 = w * (q2 - p2c), v1 = w * (q1 - p1c), vs = w * sv;
         if (EX(a) > 0) { spx += vp; s2x += v2; s1x += v1; ssx += vs; }
         if (EX(a) < 0) { spx -= vp; s2x -= v2; s1x -= v1; ssx -= vs; }
         if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(BUD_THREADS) k_budget_partial(const DevInst* _
   for (long long node = lo + threadIdx.x; node < hi; node += blockDim.x) {
     const uint8_t t = T[node] & T_MASK;
     if (is_fluid(t)) {
-      const double r1 = double(rp<R>(P).shift_f[0] + density_c<R>(F, N, node));
-      const double r2 = double(rp<R>(P).shift_f[1] + density_c<R>(F + 9 * N, N, node));
+      const double r1 = double(fshift<R>(P, 0, t) + density_c<R>(F, N, node));
+      const double r2 = double(fshift<R>(P, 1, t) + density_c<R>(F + 9 * N, N, node));
       acc[0] = fmax(acc[0], r1);
       acc[1] += r1;
       acc[2] += r2;
@@ -193,13 +194,45 @@ __global__ void __launch_bounds__(BUD_THREADS) k_budget_partial(const DevInst* _
   }
 }
 
-static __global__ void k_budget_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
-  for (int i = 0; i < NBUD; ++i) {
-    double v = (i == 0) ? -1.0 / 0.0 : 0.0;
-    for (int b = 0; b < nblocks; ++b) v = (i == 0) ? fmax(v, part[b * NBUD + i]) : v + part[b * NBUD + i];
-    out[i] = v;
+// Fixed-order reduction of the per-block budget rows (max for entry 0, sums
+// for the rest): thread t folds rows t, t + BUD_FINAL_THREADS, ... in order,
+// then a shared-memory tree combines the threads; the result depends only on
+// the rows and their count.  Valid in v[] of thread 0.
+constexpr int BUD_FINAL_THREADS = 256;
+__device__ __forceinline__ void budget_reduce(const double* __restrict__ part, int nblocks, double* v) {
+  __shared__ double sh[NBUD][BUD_FINAL_THREADS];
+  const int t = threadIdx.x;
+  double acc[NBUD];
+  acc[0] = -1.0 / 0.0;
+#pragma unroll
+  for (int i = 1; i < NBUD; ++i) acc[i] = 0.0;
+  for (int b = t; b < nblocks; b += BUD_FINAL_THREADS) {
+    acc[0] = fmax(acc[0], part[b * NBUD]);
+#pragma unroll
+    for (int i = 1; i < NBUD; ++i) acc[i] += part[b * NBUD + i];
   }
+#pragma unroll
+  for (int i = 0; i < NBUD; ++i) sh[i][t] = acc[i];
+  __syncthreads();
+  for (int s = BUD_FINAL_THREADS / 2; s > 0; s >>= 1) {
+    if (t < s) {
+      sh[0][t] = fmax(sh[0][t], sh[0][t + s]);
+#pragma unroll
+      for (int i = 1; i < NBUD; ++i) sh[i][t] += sh[i][t + s];
+    }
+    __syncthreads();
+  }
+  if (t == 0)
+#pragma unroll
+    for (int i = 0; i < NBUD; ++i) v[i] = sh[i][0];
+}
+
+static __global__ void __launch_bounds__(BUD_FINAL_THREADS) k_budget_final(const double* __restrict__ part,
+                                                                          int nblocks, double* __restrict__ out) {
+  double v[NBUD];
+  budget_reduce(part, nblocks, v);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NBUD; ++i) out[i] = v[i];
 }
 
 }  // namespace pslbm

@@ -22,6 +22,7 @@
 // to keep the hot loop small.
 #pragma once
 #include "device.cuh"
+#include "tma.cuh"
 
 namespace pslbm {
 
@@ -155,7 +156,6 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
                                             unsigned long long step, R theta, const uint8_t* s_t,
                                             const uint8_t* s_m, int eo) {
   const int node = y * P.nx + x;
-  const R sh1 = rp<R>(P).shift_f[0], sh2 = rp<R>(P).shift_f[1];
   double a_, b_;
   reservoir_rho(P, t, step, t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, node, theta), a_, b_);
   const R r1 = R(a_), r2 = R(b_);
@@ -164,7 +164,8 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
   const int dx = (t == T_INLET) ? 1 : -1;
   if (nbr(P, x, y, dx, 0, xn, yn)) {
     const int nn = yn * P.nx + xn;
-    if (is_fluid(tin[nn] & T_MASK)) {
+    const uint8_t tnn = tin[nn] & T_MASK;
+    if (is_fluid(tnn)) {
       R q1[9], q2[9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
@@ -178,7 +179,7 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
                    (q2[8] - q2[7]);
       const R jy = (q1[2] - q1[4]) + (q1[5] - q1[8]) + (q1[6] - q1[7]) + (q2[2] - q2[4]) + (q2[5] - q2[8]) +
                    (q2[6] - q2[7]);
-      const R rt = (sh1 + e1) + (sh2 + e2);
+      const R rt = (fshift<R>(P, 0, tnn) + e1) + (fshift<R>(P, 1, tnn) + e2);
       ux = jx / rt;
       uy = jy / rt;
     }
@@ -187,12 +188,13 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const R rho = s == 0 ? r1 : r2;
-    const R dr = rho - (s == 0 ? sh1 : sh2);
     TF* fo = fout + s * 9 * N;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
       const int en = eo + EY(a) * SH::EXT_X + EX(a);
       if (!is_fluid(s_t[en])) continue;
+      // stored relative to the shift of the receiving node's new phase
+      const R dr = rho - (s_m[en] ? rp<R>(P).shift_f[s] : rp<R>(P).shift_fg[s]);
       const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
       const R w = w9<R>(a);
       const R feq = w * (dr + rho * (R(3) * eu + R(4.5) * eu * eu - uu));
@@ -240,333 +242,537 @@ constexpr int bulk_min_blocks() {
   return sizeof(R) == 8 ? 2 : PSLBM_BULK_MINB;
 }
 
+// First tile at or after ti (stride `stride`) whose instance is not frozen at
+// its step limit; ntiles if none.
+__device__ __forceinline__ int next_live(const Tile* tiles, int ntiles, const DevInst* insts, int ti, int stride) {
+  for (; ti < ntiles; ti += stride) {
+    const DevInst* I = insts + tiles[ti].inst;
+    if (I->scal[S_STEP] < I->scal[S_LIMIT]) break;
+  }
+  return ti;
+}
+
+// Population source of the plain kernel: loads from global memory (L2 for
+// the ring).  own() loads the node's D2Q9 and D2Q5 populations (as stored,
+// i.e. shifted in the reduced precisions); ring_density() returns the two
+// stored density sums of a ring node.
+template <class TF, class TG, class R, int NS>
+struct GlobalSrc {
+  const TF* fin;
+  const TG* gin;
+  int N;
+  __device__ __forceinline__ void own_f(int idx, R* f1, R* f2) const {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      f1[a] = ld<R>(fin + a * N + idx);
+      f2[a] = ld<R>(fin + (9 + a) * N + idx);
+    }
+  }
+  __device__ __forceinline__ void own_g(int node, R (*gs)[5]) const {
+#pragma unroll
+    for (int k = 0; k < NS; ++k)
+#pragma unroll
+      for (int a = 0; a < 5; ++a) gs[k][a] = ld<R>(gin + (k * 5 + a) * N + node);
+  }
+  __device__ __forceinline__ void ring_density(int ring_idx, int, int, R& d1, R& d2) const {
+    d1 = density_shifted<R>(fin, (long long)N, ring_idx);
+    d2 = density_shifted<R>(fin + 9 * N, (long long)N, ring_idx);
+  }
+};
+
+// One tile of the bulk step (Sections 3-4; the order of Section 4.7 with the
+// cut after the streaming of Step 1).  `src` delivers the populations,
+// `after_sync` runs once the block has passed the tile's barrier (all reads of
+// the tile's staged populations are done by then), `tt` holds this tile's node
+// types on entry and the next tile's on return.  Returns true when the block
+// must stop (a bounded wait of the staged kernel gave up in some thread).
+template <class SH, class TF, class TG, class R, int NS, class Src, class AfterSync>
+__device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, const Src& src, AfterSync after_sync,
+                                          bool waited_ok, TileTypes& tt, const Tile* tiles, int ntiles,
+                                          const DevInst* insts, int next_ti, R* sp, R* sq1, R* sq2, uint8_t* st_,
+                                          uint8_t* sm_) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int tx = tid % SH::TX, ty = tid / SH::TX;
+  const int eo = (ty + 1) * SH::EXT_X + (tx + 1);
+  int er = -1, rex = 0, rey = 0;
+  if (tid < SH::RING) {
+    ring_pos<SH>(tid, rex, rey);
+    er = rey * SH::EXT_X + rex;
+  }
+  const DevParams& P = Ip->P;
+  const int N = (int)Ip->N;
+  const int nx = P.nx;
+  const unsigned long long step = Ip->scal[S_STEP];
+  const int cur = int(step & 1ULL);
+  const TF* __restrict__ fin = (const TF*)Ip->f[cur];
+  TF* __restrict__ fout = (TF*)Ip->f[cur ^ 1];
+  const TG* __restrict__ gin = (const TG*)Ip->g[cur];
+  TG* __restrict__ gout = (TG*)Ip->g[cur ^ 1];
+  const uint8_t* __restrict__ tin = Ip->type[cur];
+  uint8_t* __restrict__ tout = Ip->type[cur ^ 1];
+  const R theta = theta_of<R>(Ip);
+  // tiles whose ring is inside the domain need no wrap arithmetic
+  const bool inner = tl.x0 >= 1 && tl.y0 >= 1 && tl.x0 + SH::TX + 1 <= nx && tl.y0 + SH::TY + 1 <= P.ny;
+  unsigned status = 0;
+
+  // ---- phase 1: population loads (own node and one ring node)
+  const int x = tl.x0 + tx, y = tl.y0 + ty;
+  const bool own = x < nx && y < P.ny;
+  const int node = y * nx + x;
+  const uint8_t own_t = tt.own;
+  const uint8_t ring_t = tt.ring;
+  const int own_idx = tt.own_idx, ring_idx = tt.ring_idx;
+  const uint8_t t = own ? own_t : T_WALL;
+  // populations are stored relative to the reference density of the node's
+  // phase (0 in FP64)
+  const R sh1 = fshift<R>(P, 0, own_t), sh2 = fshift<R>(P, 1, own_t);
+  R f1[9], f2[9];
+  R gs[NS > 0 ? NS : 1][5];
+  const bool own_fluid = is_fluid(own_t) && own_idx >= 0;
+  if (own_fluid) src.own_f(own_idx, f1, f2);
+  if constexpr (NS > 0) {
+    if (own && own_t == T_LIQUID) src.own_g(node, gs);
+  }
+  R r1r = R(0), r2r = R(0);
+  if (tid < SH::RING && is_fluid(ring_t)) {
+    R d1r, d2r;
+    src.ring_density(ring_idx, tl.x0 - 1 + rex, tl.y0 - 1 + rey, d1r, d2r);
+    r1r = fshift<R>(P, 0, ring_t) + d1r;
+    r2r = fshift<R>(P, 1, ring_t) + d2r;
+  }
+  // prefetch the next tile's node types
+  if (next_ti < ntiles) tt = load_types<SH>(tiles, insts, next_ti, tid);
+
+  // ---- moments of the own node (Eq. 9), potentials -> shared
+  R rho1 = R(0), rho2 = R(0), d1 = R(0), d2 = R(0), j1x = R(0), j1y = R(0), j2x = R(0), j2y = R(0);
+  {
+    R r1 = R(0), r2 = R(0);
+    if (own_fluid) {
+      d1 = f1[0];
+      d2 = f2[0];
+#pragma unroll
+      for (int a = 1; a < 9; ++a) {
+        d1 += f1[a];
+        d2 += f2[a];
+      }
+      j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
+      j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
+      j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
+      j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
+      rho1 = sh1 + d1;
+      rho2 = sh2 + d2;
+      r1 = rho1;
+      r2 = rho2;
+      if (!(rho1 == rho1 && rho2 == rho2)) status |= ST_NONFINITE;
+    } else if (is_res(own_t)) {
+      double a, b;
+      reservoir_rho(P, own_t, step, own_t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, own_idx, theta),
+                    a, b);
+      r1 = R(a);
+      r2 = R(b);
+    }
+    R ps = R(0), p1 = R(0), p2 = R(0);
+    if (is_live(own_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
+    sp[eo] = ps;
+    sq1[eo] = p1;
+    sq2[eo] = p2;
+    st_[eo] = own_t;
+    sm_[eo] = (is_live(own_t) && r1 > theta) ? 1 : 0;
+  }
+  if (tid < SH::RING) {
+    R r1 = r1r, r2 = r2r;
+    if (is_res(ring_t)) {
+      double a, b;
+      reservoir_rho(P, ring_t, step, ring_t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, ring_idx, theta),
+                    a, b);
+      r1 = R(a);
+      r2 = R(b);
+    }
+    R ps = R(0), p1 = R(0), p2 = R(0);
+    if (is_live(ring_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
+    sp[er] = ps;
+    sq1[er] = p1;
+    sq2[er] = p2;
+    st_[er] = ring_t;
+    sm_[er] = (is_live(ring_t) && r1 > theta) ? 1 : 0;
+  }
+  if (__syncthreads_or(waited_ok ? 0 : 1)) return true;
+  after_sync();
+
+  R mymax = R(-1.0 / 0.0);
+  if (own && is_fluid(t)) {
+    mymax = rho1;
+    // ---- forces (Eqs. 11, 14a/b, 16) with neutral solid neighbours.  The
+    // stencils sum w (value(x + e) - value(x)) e, equal to the sums of Eqs. 11
+    // and 14 since sum_a w e = 0, but free of the cancellation between nearly
+    // equal neighbour values in a bulk phase; a solid neighbour contributes 0.
+    const R psc = sp[eo], p1c = sq1[eo], p2c = sq2[eo];
+    R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+      const int en = eo + EY(a) * SH::EXT_X + EX(a);
+      const bool lv = is_live(st_[en]);
+      const R w = wf<R>(a);
+      const R vp = lv ? w * (sp[en] - psc) : R(0);
+      const R v2 = lv ? w * (sq2[en] - p2c) : R(0);
+      const R v1 = lv ? w * (sq1[en] - p1c) : R(0);
+      const R vs = lv ? R(0) : w;
+      if (EX(a) > 0) { spx += vp; s2x += v2; s1x += v1; ssx += vs; }
+      if (EX(a) < 0) { spx -= vp; s2x -= v2; s1x -= v1; ssx -= vs; }
+      if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
+      if (EY(a) < 0) { spy -= vp; s2y -= v2; s1y -= v1; ssy -= vs; }
+    }
+    const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0],
+            w2 = rp<R>(P).w_adh[1];
+    const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * rp<R>(P).gx;
+    const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * rp<R>(P).gy;
+    const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * rp<R>(P).gx;
+    const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * rp<R>(P).gy;
+    // ---- velocities (Eqs. 17-19)
+    const R it1 = rp<R>(P).inv_tau[0], it2 = rp<R>(P).inv_tau[1];
+    const R rden = rrcp<R>(rho1 * it1 + rho2 * it2);
+    const R upx = (j1x * it1 + j2x * it2) * rden;
+    const R upy = (j1y * it1 + j2y * it2) * rden;
+    const R q1 = rho1 != R(0) ? rp<R>(P).tau[0] * rrcp<R>(rho1) : R(0);
+    const R q2 = rho2 != R(0) ? rp<R>(P).tau[1] * rrcp<R>(rho2) : R(0);
+    const R u1x = upx + F1x * q1, u1y = upy + F1y * q1;
+    const R u2x = upx + F2x * q2, u2y = upy + F2y * q2;
+    const R rrt = rrcp<R>(rho1 + rho2);
+    const R urx = (j1x + j2x + R(0.5) * (F1x + F2x)) * rrt;
+    const R ury = (j1y + j2y + R(0.5) * (F1y + F2y)) * rrt;
+
+    const bool liq = sm_[eo] != 0;
+    tout[node] = liq ? T_LIQUID : T_GAS;
+
+    // neighbour indices for the push (constant offsets away from the edges)
+    int nb[9];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) nb[a] = inner ? node + EX(a) + EY(a) * nx : nbr_index(P, x, y, EX(a), EY(a));
+
+    // ---- solutes: concentration with the Step-2 amendment, sources
+    R S1 = R(0), S2 = R(0);
+    R C[NS > 0 ? NS : 1];
+    R Sk[NS > 0 ? NS : 1];
+    if constexpr (NS > 0) {
+      if (liq) {
+        const bool appear = (t == T_GAS);
+        bool vnb = false;
+#pragma unroll
+        for (int b = 1; b < 5; ++b) {
+          const int en = eo + EY(b) * SH::EXT_X + EX(b);
+          vnb |= (st_[en] == T_LIQUID && sm_[en] == 0);
+        }
+        if (appear || vnb) {
+          R dC[NS], cb[NS];
+          amend_marking<SH, R, TF, TG, NS>(P, tin, fin, gin, N, x, y, appear, st_, sm_, eo, theta, dC, cb);
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            const R J0 = rp<R>(P).J0[k], Ja = rp<R>(P).Ja[k];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+              const R ja = a == 0 ? J0 : Ja;
+              gs[k][a] = appear ? ja * (cb[k] + dC[k]) - ja * rp<R>(P).shift_c[k] : gs[k][a] + ja * dC[k];
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          R s = gs[k][0];
+#pragma unroll
+          for (int a = 1; a < 5; ++a) s += gs[k][a];
+          C[k] = rp<R>(P).shift_c[k] + s;
+        }
+        // homogeneous reactions (Eqs. 5a, 5c; sources Eqs. 27, 28)
+        R CA = R(0), CB = R(0), CE = R(0), tot = R(0);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          if (k == P.iA) CA = C[k];
+          if (k == P.iB) CB = C[k];
+          if (k == P.iE) CE = C[k];
+          tot += C[k];
+        }
+        if (P.iA == -2) CA = rmax<R>(R(0), rp<R>(P).c_total_per_rho1 * rho1 - tot);
+        R R1 = rp<R>(P).k1 * CA;
+        if (P.has_rev) R1 -= rp<R>(P).k1_inv_Keq * CB * rsqrt_<R>(rmax<R>(rho2 * rp<R>(P).inv_M_C, R(0)));
+        const R R3 = rp<R>(P).k3 * CB * CE;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) Sk[k] = rp<R>(P).cR1[k] * R1 + rp<R>(P).cR3[k] * R3;
+        S1 = -rp<R>(P).gas_yield * R1;
+        S2 = rp<R>(P).gas_yield * R1;
+      }
+    }
+
+    // ---- fluid collision (Eq. 6, Eq. 8 at u_eq) and push streaming.  The
+    // collision runs relative to this node's shift; a value pushed into a node
+    // whose new phase has another shift is re-based by w (shift - shift').
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const R rho = s == 0 ? rho1 : rho2;
+      const R dr = s == 0 ? d1 : d2;
+      const R ux = s == 0 ? u1x : u2x, uy = s == 0 ? u1y : u2y;
+      const R itau = s == 0 ? it1 : it2;
+      const R Ssrc = s == 0 ? S1 : S2;
+      const R uu = R(1.5) * (ux * ux + uy * uy);
+      const R shs = s == 0 ? sh1 : sh2;
+      const R dl = shs - rp<R>(P).shift_f[s], dg = shs - rp<R>(P).shift_fg[s];
+      const R down = liq ? dl : dg;
+      TF* fo = fout + s * 9 * N;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const R fa = s == 0 ? f1[a] : f2[a];
+        const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
+        const R w = w9<R>(a);
+        const R feq = w * (dr + rho * (R(3) * eu + R(4.5) * eu * eu - uu));
+        const R fs = fa - (fa - feq) * itau + w * Ssrc;
+        if (a == 0) {
+          st<TF, R>(fo + node, fs + w * down);
+          continue;
+        }
+        const int en = eo + EY(a) * SH::EXT_X + EX(a);
+        const uint8_t tn = st_[en];
+        if (is_fluid(tn))
+          st<TF, R>(fo + a * N + nb[a], fs + w * (sm_[en] ? dl : dg));
+        else if (!is_res(tn))
+          st<TF, R>(fo + OPP(a) * N + node, fs + w * down);
+      }
+    }
+
+    // ---- solute collision (Eqs. 20-22 with u_r) and push streaming
+    if constexpr (NS > 0) {
+      if (liq) {
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          const R eu = R(EX(a)) * urx + R(EY(a)) * ury;
+          int dst = node, slot = a;            // rest population stays
+          bool keep = true;
+          if (a > 0) {
+            const int en = eo + EY(a) * SH::EXT_X + EX(a);
+            const uint8_t tn = st_[en];
+            const bool mn = sm_[en] != 0;
+            if (is_fluid(tn) && mn) {
+              dst = nb[a];                     // into a liquid neighbour
+            } else if (is_res(tn) && mn) {
+              keep = false;                    // outflow into a liquid reservoir
+            } else {
+              slot = OPP(a);                   // no-flux / mineral: bounce back
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+            const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
+            const R geq = ja * (C[k] - rp<R>(P).shift_c[k]) + R(0.5) * C[k] * eu;
+            const R gst = gs[k][a] - (gs[k][a] - geq) * rp<R>(P).inv_tau_g[k] + ja * Sk[k];
+            if (keep) st<TG, R>(gout + (k * 5 + slot) * N + dst, gst);
+          }
+        }
+      } else {
+        // gas node: no solute
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+#pragma unroll
+          for (int a = 0; a < 5; ++a)
+            st<TG, R>(gout + (k * 5 + a) * N + node,
+                      -(a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k]) * rp<R>(P).shift_c[k]);
+        }
+      }
+    }
+  } else if (own) {
+    if (is_res(t))
+      reservoir_push<SH, R, TF, TG, NS>(P, tin, fin, gin, fout, gout, N, x, y, t, step, theta, st_, sm_, eo);
+    tout[node] = t;
+  }
+
+  // ---- warp max of rho_1 over fluid nodes (next step's threshold) and status
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mymax = rmax<R>(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+  status = __reduce_or_sync(0xffffffffu, status);
+  if (lane == 0) {
+    if (mymax > R(-1.0 / 0.0)) {
+      // exact maximum; the atomic only when it can raise the slot
+      const unsigned long long enc = ord_enc(double(mymax));
+      unsigned long long* slot = &Ip->scal[S_MAX0 + (cur ^ 1)];
+      if (enc > *(volatile unsigned long long*)slot) atomicMax(slot, enc);
+    }
+    if (status) atomicOr(&Ip->scal[S_STATUS], (unsigned long long)status);
+  }
+  return false;
+}
+
+// Plain bulk kernel: persistent over the tile list, populations loaded from
+// global memory by each thread.  The shared stage is double-buffered, so a
+// tile costs one block barrier.
 template <class SH, class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const Tile* __restrict__ tiles, int ntiles,
                                                                          const DevInst* __restrict__ insts) {
   __shared__ R s_psi[2][SH::EXT], s_phi1[2][SH::EXT], s_phi2[2][SH::EXT];
   __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int tx = tid % SH::TX, ty = tid / SH::TX;
-  const int eo = (ty + 1) * SH::EXT_X + (tx + 1);
-  int er = -1;
-  if (tid < SH::RING) {
-    int ex, ey;
-    ring_pos<SH>(tid, ex, ey);
-    er = ey * SH::EXT_X + ex;
-  }
-
-  int ti = blockIdx.x;
+  int ti = next_live(tiles, ntiles, insts, blockIdx.x, gridDim.x);
   int buf = 0;
   TileTypes tt;
-  if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, tid);
-
-  for (; ti < ntiles; ti += gridDim.x) {
+  if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, threadIdx.x);
+  while (ti < ntiles) {
+    const int nt = next_live(tiles, ntiles, insts, ti + gridDim.x, gridDim.x);
     const Tile tl = tiles[ti];
     const DevInst* Ip = insts + tl.inst;
-    const DevParams& P = Ip->P;
-    const int N = (int)Ip->N;
-    const int nx = P.nx;
-    const unsigned long long step = Ip->scal[S_STEP];
-    if (step >= Ip->scal[S_LIMIT]) {
-      // frozen instance: keep the type prefetch in step with the tile walk; the
-      // stage buffer is not toggled, so no barrier is skipped for it
-      if (ti + (int)gridDim.x < ntiles) tt = load_types<SH>(tiles, insts, ti + gridDim.x, tid);
-      continue;
-    }
-    const int cur = int(step & 1ULL);
-    const TF* __restrict__ fin = (const TF*)Ip->f[cur];
-    TF* __restrict__ fout = (TF*)Ip->f[cur ^ 1];
-    const TG* __restrict__ gin = (const TG*)Ip->g[cur];
-    TG* __restrict__ gout = (TG*)Ip->g[cur ^ 1];
-    const uint8_t* __restrict__ tin = Ip->type[cur];
-    uint8_t* __restrict__ tout = Ip->type[cur ^ 1];
-    const R theta = R(0.5 * ord_dec(Ip->scal[S_MAX0 + cur]));
-    const R sh1 = rp<R>(P).shift_f[0], sh2 = rp<R>(P).shift_f[1];
-    // tiles whose ring is inside the domain need no wrap arithmetic
-    const bool inner = tl.x0 >= 1 && tl.y0 >= 1 && tl.x0 + SH::TX + 1 <= nx && tl.y0 + SH::TY + 1 <= P.ny;
-    R* sp = s_psi[buf];
-    R* sq1 = s_phi1[buf];
-    R* sq2 = s_phi2[buf];
-    uint8_t* st_ = s_t[buf];
-    uint8_t* sm_ = s_m[buf];
-    unsigned status = 0;
+    const int cur = int(Ip->scal[S_STEP] & 1ULL);
+    const GlobalSrc<TF, TG, R, NS> src{(const TF*)Ip->f[cur], (const TG*)Ip->g[cur], (int)Ip->N};
+    bulk_tile<SH, TF, TG, R, NS>(tl, Ip, src, [] {}, true, tt, tiles, ntiles, insts, nt, s_psi[buf], s_phi1[buf],
+                                 s_phi2[buf], s_t[buf], s_m[buf]);
+    buf ^= 1;
+    ti = nt;
+  }
+}
 
-    // ---- phase 1: issue population loads (own node and one ring node)
-    const int x = tl.x0 + tx, y = tl.y0 + ty;
-    const bool own = x < nx && y < P.ny;
-    const int node = y * nx + x;
-    const uint8_t own_t = tt.own;
-    const uint8_t ring_t = tt.ring;
-    const int own_idx = tt.own_idx, ring_idx = tt.ring_idx;
-    const uint8_t t = own ? own_t : T_WALL;
-    R f1[9], f2[9];
-    R gs[NS > 0 ? NS : 1][5];
-    const bool own_fluid = is_fluid(own_t) && own_idx >= 0;
-    if (own_fluid) {
+// ---------------------------------------------------------------- staged
+
+// Shared-memory stage of the staged kernel: the D2Q9 box of a tile (both
+// components, the tile plus a ring of one node in y and four in x, so that
+// the box's x origin stays on a 16-byte boundary) and the D2Q5 box of the
+// tile itself, as the TMA unit writes them (x fastest, then y, then plane).
+template <class SH, class TG, int NS>
+struct StageCfg {
+  static constexpr int BX = SH::TX + 2 * STAGE_HALO_X, BY = SH::TY + 2;
+  static constexpr int FBYTES = BX * BY * 18 * 4;
+  static constexpr int GBYTES = NS > 0 ? SH::TX * SH::TY * 5 * NS * (int)sizeof(TG) : 0;
+  static constexpr int FOFF = 0;
+  static constexpr int GOFF = ((FBYTES + 127) / 128) * 128;
+  static constexpr int STAGE = GOFF + ((GBYTES + 127) / 128) * 128;
+  static constexpr int SMEM = 2 * STAGE;
+  static constexpr uint32_t TX_BYTES = FBYTES + GBYTES;
+};
+
+// Population source of the staged kernel: the tile's own populations and the
+// ring densities come from the shared stage; nodes that lie across a periodic
+// edge (outside the box) are read from global memory.
+template <class SH, class TG, int NS>
+struct StageSrc {
+  using C = StageCfg<SH, TG, NS>;
+  const float* fs;     // stage D2Q9 box
+  const TG* gs_;       // stage D2Q5 box
+  const float* fin;
+  int N, nx, ny, x0, y0;
+  // A thread position beyond the lattice edge of a partial tile stands for the
+  // wrapped node across a periodic edge (idx >= 0 only then): not in the box.
+  __device__ __forceinline__ void own_f(int idx, float* f1, float* f2) const {
+    const int tx = threadIdx.x % SH::TX, ty = threadIdx.x / SH::TX;
+    if (x0 + tx < nx && y0 + ty < ny) {
+      const float* b = fs + (ty + 1) * C::BX + (tx + STAGE_HALO_X);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        f1[a] = ld<R>(fin + a * N + own_idx);
-        f2[a] = ld<R>(fin + (9 + a) * N + own_idx);
+        f1[a] = b[a * C::BX * C::BY];
+        f2[a] = b[(9 + a) * C::BX * C::BY];
       }
-    }
-    if constexpr (NS > 0) {
-      if (own && own_t == T_LIQUID) {
+    } else {
 #pragma unroll
-        for (int k = 0; k < NS; ++k)
+      for (int a = 0; a < 9; ++a) {
+        f1[a] = ld<float>(fin + a * N + idx);
+        f2[a] = ld<float>(fin + (9 + a) * N + idx);
+      }
+    }
+  }
+  __device__ __forceinline__ void own_g(int, float (*g)[5]) const {
+    const int i = threadIdx.x;
 #pragma unroll
-          for (int a = 0; a < 5; ++a) gs[k][a] = ld<R>(gin + (k * 5 + a) * N + node);
-      }
-    }
-    R r1r = R(0), r2r = R(0);
-    if (tid < SH::RING && is_fluid(ring_t)) {
-      r1r = sh1 + density_shifted<R>(fin, (long long)N, ring_idx);
-      r2r = sh2 + density_shifted<R>(fin + 9 * N, (long long)N, ring_idx);
-    }
-    // prefetch the next tile's node types
-    if (ti + (int)gridDim.x < ntiles) tt = load_types<SH>(tiles, insts, ti + gridDim.x, tid);
-
-    // ---- moments of the own node (Eq. 9), potentials -> shared
-    R rho1 = R(0), rho2 = R(0), d1 = R(0), d2 = R(0), j1x = R(0), j1y = R(0), j2x = R(0), j2y = R(0);
-    {
-      R r1 = R(0), r2 = R(0);
-      if (own_fluid) {
-        d1 = f1[0];
-        d2 = f2[0];
+    for (int k = 0; k < NS; ++k)
 #pragma unroll
-        for (int a = 1; a < 9; ++a) {
-          d1 += f1[a];
-          d2 += f2[a];
-        }
-        j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
-        j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
-        j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
-        j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
-        rho1 = sh1 + d1;
-        rho2 = sh2 + d2;
-        r1 = rho1;
-        r2 = rho2;
-        if (!(rho1 == rho1 && rho2 == rho2)) status |= ST_NONFINITE;
-      } else if (is_res(own_t)) {
-        double a, b;
-        reservoir_rho(P, own_t, step,
-                      own_t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, own_idx, theta), a, b);
-        r1 = R(a);
-        r2 = R(b);
-      }
-      R ps = R(0), p1 = R(0), p2 = R(0);
-      if (is_live(own_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
-      sp[eo] = ps;
-      sq1[eo] = p1;
-      sq2[eo] = p2;
-      st_[eo] = own_t;
-      sm_[eo] = (is_live(own_t) && r1 > theta) ? 1 : 0;
-    }
-    if (tid < SH::RING) {
-      R r1 = r1r, r2 = r2r;
-      if (is_res(ring_t)) {
-        double a, b;
-        reservoir_rho(P, ring_t, step,
-                      ring_t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, ring_idx, theta), a, b);
-        r1 = R(a);
-        r2 = R(b);
-      }
-      R ps = R(0), p1 = R(0), p2 = R(0);
-      if (is_live(ring_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
-      sp[er] = ps;
-      sq1[er] = p1;
-      sq2[er] = p2;
-      st_[er] = ring_t;
-      sm_[er] = (is_live(ring_t) && r1 > theta) ? 1 : 0;
-    }
-    __syncthreads();
-
-    R mymax = R(-1.0 / 0.0);
-    if (own && is_fluid(t)) {
-      mymax = rho1;
-      // ---- forces (Eqs. 11, 14a/b, 16) with neutral solid neighbours
-      const R psc = sp[eo], p1c = sq1[eo], p2c = sq2[eo];
-      R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
+      for (int a = 0; a < 5; ++a) g[k][a] = ldc<float>(gs_ + (k * 5 + a) * SH::TX * SH::TY + i);
+  }
+  __device__ __forceinline__ void ring_density(int ring_idx, int rx, int ry, float& d1, float& d2) const {
+    if (rx >= 0 && rx < nx && ry >= 0 && ry < ny) {
+      const float* b = fs + (ry - y0 + 1) * C::BX + (rx - x0 + STAGE_HALO_X);
+      float s1 = b[0], s2 = b[9 * C::BX * C::BY];
 #pragma unroll
       for (int a = 1; a < 9; ++a) {
-        const int en = eo + EY(a) * SH::EXT_X + EX(a);
-        const bool lv = is_live(st_[en]);
-        const R w = wf<R>(a);
-        const R vp = w * (lv ? sp[en] : psc);
-        const R v2 = w * (lv ? sq2[en] : p2c);
-        const R v1 = w * (lv ? sq1[en] : p1c);
-        const R vs = lv ? R(0) : w;
-        if (EX(a) > 0) { spx += vp; s2x += v2; s1x += v1; ssx += vs; }
-        if (EX(a) < 0) { spx -= vp; s2x -= v2; s1x -= v1; ssx -= vs; }
-        if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
-        if (EY(a) < 0) { spy -= vp; s2y -= v2; s1y -= v1; ssy -= vs; }
+        s1 += b[a * C::BX * C::BY];
+        s2 += b[(9 + a) * C::BX * C::BY];
       }
-      const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0], w2 = rp<R>(P).w_adh[1];
-      const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * rp<R>(P).gx;
-      const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * rp<R>(P).gy;
-      const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * rp<R>(P).gx;
-      const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * rp<R>(P).gy;
-      // ---- velocities (Eqs. 17-19)
-      const R it1 = rp<R>(P).inv_tau[0], it2 = rp<R>(P).inv_tau[1];
-      const R rden = rrcp<R>(rho1 * it1 + rho2 * it2);
-      const R upx = (j1x * it1 + j2x * it2) * rden;
-      const R upy = (j1y * it1 + j2y * it2) * rden;
-      const R q1 = rho1 != R(0) ? rp<R>(P).tau[0] * rrcp<R>(rho1) : R(0);
-      const R q2 = rho2 != R(0) ? rp<R>(P).tau[1] * rrcp<R>(rho2) : R(0);
-      const R u1x = upx + F1x * q1, u1y = upy + F1y * q1;
-      const R u2x = upx + F2x * q2, u2y = upy + F2y * q2;
-      const R rrt = rrcp<R>(rho1 + rho2);
-      const R urx = (j1x + j2x + R(0.5) * (F1x + F2x)) * rrt;
-      const R ury = (j1y + j2y + R(0.5) * (F1y + F2y)) * rrt;
-
-      const bool liq = sm_[eo] != 0;
-      tout[node] = liq ? T_LIQUID : T_GAS;
-
-      // neighbour indices for the push (constant offsets away from the edges)
-      int nb[9];
-#pragma unroll
-      for (int a = 1; a < 9; ++a) nb[a] = inner ? node + EX(a) + EY(a) * nx : nbr_index(P, x, y, EX(a), EY(a));
-
-      // ---- solutes: concentration with the Step-2 amendment, sources
-      R S1 = R(0), S2 = R(0);
-      R C[NS > 0 ? NS : 1];
-      R Sk[NS > 0 ? NS : 1];
-      if constexpr (NS > 0) {
-        if (liq) {
-          const bool appear = (t == T_GAS);
-          bool vnb = false;
-#pragma unroll
-          for (int b = 1; b < 5; ++b) {
-            const int en = eo + EY(b) * SH::EXT_X + EX(b);
-            vnb |= (st_[en] == T_LIQUID && sm_[en] == 0);
-          }
-          if (appear || vnb) {
-            R dC[NS], cb[NS];
-            amend_marking<SH, R, TF, TG, NS>(P, tin, fin, gin, N, x, y, appear, st_, sm_, eo, theta, dC, cb);
-#pragma unroll
-            for (int k = 0; k < NS; ++k) {
-              const R J0 = rp<R>(P).J0[k], Ja = rp<R>(P).Ja[k];
-#pragma unroll
-              for (int a = 0; a < 5; ++a) {
-                const R ja = a == 0 ? J0 : Ja;
-                gs[k][a] = appear ? ja * (cb[k] + dC[k]) - ja * rp<R>(P).shift_c[k] : gs[k][a] + ja * dC[k];
-              }
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < NS; ++k) {
-            R s = gs[k][0];
-#pragma unroll
-            for (int a = 1; a < 5; ++a) s += gs[k][a];
-            C[k] = rp<R>(P).shift_c[k] + s;
-          }
-          // homogeneous reactions (Eqs. 5a, 5c; sources Eqs. 27, 28)
-          R CA = R(0), CB = R(0), CE = R(0), tot = R(0);
-#pragma unroll
-          for (int k = 0; k < NS; ++k) {
-            if (k == P.iA) CA = C[k];
-            if (k == P.iB) CB = C[k];
-            if (k == P.iE) CE = C[k];
-            tot += C[k];
-          }
-          if (P.iA == -2) CA = rmax<R>(R(0), rp<R>(P).c_total_per_rho1 * rho1 - tot);
-          R R1 = rp<R>(P).k1 * CA;
-          if (P.has_rev) R1 -= rp<R>(P).k1_inv_Keq * CB * rsqrt_<R>(rmax<R>(rho2 * rp<R>(P).inv_M_C, R(0)));
-          const R R3 = rp<R>(P).k3 * CB * CE;
-#pragma unroll
-          for (int k = 0; k < NS; ++k) Sk[k] = rp<R>(P).cR1[k] * R1 + rp<R>(P).cR3[k] * R3;
-          S1 = -rp<R>(P).gas_yield * R1;
-          S2 = rp<R>(P).gas_yield * R1;
-        }
-      }
-
-      // ---- fluid collision (Eq. 6, Eq. 8 at u_eq) and push streaming
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const R rho = s == 0 ? rho1 : rho2;
-        const R dr = s == 0 ? d1 : d2;
-        const R ux = s == 0 ? u1x : u2x, uy = s == 0 ? u1y : u2y;
-        const R itau = s == 0 ? it1 : it2;
-        const R Ssrc = s == 0 ? S1 : S2;
-        const R uu = R(1.5) * (ux * ux + uy * uy);
-        TF* fo = fout + s * 9 * N;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-          const R fa = s == 0 ? f1[a] : f2[a];
-          const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
-          const R w = w9<R>(a);
-          const R feq = w * (dr + rho * (R(3) * eu + R(4.5) * eu * eu - uu));
-          const R fs = fa - (fa - feq) * itau + w * Ssrc;
-          if (a == 0) {
-            st<TF, R>(fo + node, fs);
-            continue;
-          }
-          const uint8_t tn = st_[eo + EY(a) * SH::EXT_X + EX(a)];
-          if (is_fluid(tn))
-            st<TF, R>(fo + a * N + nb[a], fs);
-          else if (!is_res(tn))
-            st<TF, R>(fo + OPP(a) * N + node, fs);
-        }
-      }
-
-      // ---- solute collision (Eqs. 20-22 with u_r) and push streaming
-      if constexpr (NS > 0) {
-        if (liq) {
-#pragma unroll
-          for (int a = 0; a < 5; ++a) {
-            const R eu = R(EX(a)) * urx + R(EY(a)) * ury;
-            int dst = node, slot = a;            // rest population stays
-            bool keep = true;
-            if (a > 0) {
-              const int en = eo + EY(a) * SH::EXT_X + EX(a);
-              const uint8_t tn = st_[en];
-              const bool mn = sm_[en] != 0;
-              if (is_fluid(tn) && mn) {
-                dst = nb[a];                     // into a liquid neighbour
-              } else if (is_res(tn) && mn) {
-                keep = false;                    // outflow into a liquid reservoir
-              } else {
-                slot = OPP(a);                   // no-flux / mineral: bounce back
-              }
-            }
-#pragma unroll
-            for (int k = 0; k < NS; ++k) {
-              const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
-              const R geq = ja * (C[k] - rp<R>(P).shift_c[k]) + R(0.5) * C[k] * eu;
-              const R gst = gs[k][a] - (gs[k][a] - geq) * rp<R>(P).inv_tau_g[k] + ja * Sk[k];
-              if (keep) st<TG, R>(gout + (k * 5 + slot) * N + dst, gst);
-            }
-          }
-        } else {
-          // gas node: no solute
-#pragma unroll
-          for (int k = 0; k < NS; ++k) {
-#pragma unroll
-            for (int a = 0; a < 5; ++a)
-              st<TG, R>(gout + (k * 5 + a) * N + node, -(a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k]) * rp<R>(P).shift_c[k]);
-          }
-        }
-      }
-    } else if (own) {
-      if (is_res(t)) reservoir_push<SH, R, TF, TG, NS>(P, tin, fin, gin, fout, gout, N, x, y, t, step, theta, st_, sm_, eo);
-      tout[node] = t;
+      d1 = s1;
+      d2 = s2;
+    } else {
+      d1 = density_shifted<float>(fin, (long long)N, ring_idx);
+      d2 = density_shifted<float>(fin + 9 * N, (long long)N, ring_idx);
     }
+  }
+};
 
-    // ---- warp max of rho_1 over fluid nodes (next step's threshold) and status
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mymax = rmax<R>(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
-    status = __reduce_or_sync(0xffffffffu, status);
-    if (lane == 0) {
-      if (mymax > R(-1.0 / 0.0)) {
-        // exact maximum; the atomic only when it can raise the slot
-        const unsigned long long enc = ord_enc(double(mymax));
-        unsigned long long* slot = &Ip->scal[S_MAX0 + (cur ^ 1)];
-        if (enc > *(volatile unsigned long long*)slot) atomicMax(slot, enc);
+// Issue the TMA copies of tile `ti` into a stage (one thread).
+template <class SH, class TG, int NS, int SHAPE>
+__device__ __forceinline__ void stage_issue(const Tile* tiles, const DevInst* insts, int ti, unsigned char* stage,
+                                            uint64_t* bar) {
+  using C = StageCfg<SH, TG, NS>;
+  const Tile tl = tiles[ti];
+  const DevInst* Ip = insts + tl.inst;
+  const int cur = int(Ip->scal[S_STEP] & 1ULL);
+  const CUtensorMap* mf = &Ip->tmf[SHAPE][cur];
+  const CUtensorMap* mg = &Ip->tmg[SHAPE][cur];
+  tensormap_acquire(mf);
+  if constexpr (NS > 0) tensormap_acquire(mg);
+  mbar_arrive_expect_tx(bar, C::TX_BYTES);
+  tma_load_3d(stage + C::FOFF, mf, bar, tl.x0 - STAGE_HALO_X, tl.y0 - 1, 0);
+  if constexpr (NS > 0) tma_load_3d(stage + C::GOFF, mg, bar, tl.x0, tl.y0, 0);
+}
+
+// Staged bulk kernel (FP32 populations): while the block computes tile j, the
+// TMA unit brings tiles j+1 and j+2 into the two shared stages, so the
+// populations' DRAM latency overlaps arithmetic instead of stalling it.  The
+// arithmetic is the plain kernel's, value for value.
+template <class SH, int SHAPE, class TG, int NS>
+__global__ void __launch_bounds__(NTHREADS, 2) k_bulk_tma(const Tile* __restrict__ tiles, int ntiles,
+                                                          const DevInst* __restrict__ insts) {
+  using C = StageCfg<SH, TG, NS>;
+  using R = float;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ R s_psi[2][SH::EXT], s_phi1[2][SH::EXT], s_phi2[2][SH::EXT];
+  __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
+  __shared__ __align__(8) uint64_t bars[2];
+
+  const int stride = gridDim.x;
+  int ti = next_live(tiles, ntiles, insts, blockIdx.x, stride);
+  int t1 = ti < ntiles ? next_live(tiles, ntiles, insts, ti + stride, stride) : ntiles;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (ti < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, ti, dyn, &bars[0]);
+    if (t1 < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, t1, dyn + C::STAGE, &bars[1]);
+  }
+  TileTypes tt;
+  if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, threadIdx.x);
+  int j = 0;                        // tiles processed by this block
+  uint32_t phase = 0;               // parity bit per stage
+  while (ti < ntiles) {
+    const int b = j & 1;
+    const int t2 = t1 < ntiles ? next_live(tiles, ntiles, insts, t1 + stride, stride) : ntiles;
+    const bool ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
+    phase ^= 1u << b;
+    const Tile tl = tiles[ti];
+    const DevInst* Ip = insts + tl.inst;
+    const int cur = int(Ip->scal[S_STEP] & 1ULL);
+    unsigned char* stage = dyn + b * C::STAGE;
+    const StageSrc<SH, TG, NS> src{(const float*)(stage + C::FOFF), (const TG*)(stage + C::GOFF),
+                                   (const float*)Ip->f[cur], (int)Ip->N, Ip->P.nx, Ip->P.ny, tl.x0, tl.y0};
+    // after the tile's barrier its stage is free: refill it with tile j+2
+    auto refill = [&] {
+      if (threadIdx.x == 0 && t2 < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, t2, stage, &bars[b]);
+    };
+    if (bulk_tile<SH, float, TG, R, NS>(tl, Ip, src, refill, ok, tt, tiles, ntiles, insts, t1, s_psi[b], s_phi1[b],
+                                        s_phi2[b], s_t[b], s_m[b])) {
+      // a wait gave up: record it, let the copies still in flight land
+      // (bounded waits: this tile's stage, and the next tile's), and leave
+      if (threadIdx.x == 0) {
+        atomicOr(&Ip->scal[S_STATUS], (unsigned long long)ST_TIMEOUT);
+        mbar_wait_bounded(&bars[b], ((phase >> b) & 1u) ^ 1u);
+        if (t1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
       }
-      if (status) atomicOr(&Ip->scal[S_STATUS], (unsigned long long)status);
+      return;
     }
-    buf ^= 1;
+    ++j;
+    ti = t1;
+    t1 = t2;
   }
 }
 

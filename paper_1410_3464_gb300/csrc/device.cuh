@@ -2,6 +2,7 @@
 // LBM (Chen, Kang et al., arXiv 1410.3464, Sections 3-4).
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -33,6 +34,10 @@ using ShapeB = TileShape<32, 8>;
 constexpr int NSHAPES = 2;
 constexpr int SHAPE_TX[NSHAPES] = {ShapeA::TX, ShapeB::TX};
 constexpr int SHAPE_TY[NSHAPES] = {ShapeA::TY, ShapeB::TY};
+// The staged bulk kernel's D2Q9 box reaches this many nodes left and right of
+// its tile (one ring node is needed; four keep the box's x origin on a 16-byte
+// boundary for FP32 rows), and one node above and below.
+constexpr int STAGE_HALO_X = 4;
 
 // Per-instance scalar slots (unsigned long long each).
 enum {
@@ -42,9 +47,11 @@ enum {
   S_STATUS = 3,    // error bits
   S_NEVENT = 4,    // events recorded by the VOP kernel this step
   S_LIMIT = 5,     // step limit: an instance at or past it is frozen (kernels skip it)
+  S_THETA = 6,     // this step's liquid threshold (half the previous maximum), FP64 bits
+  S_THETAF = 7,    // the same rounded to FP32 (bits in the low word)
   S_NSCAL = 8
 };
-enum { ST_NONFINITE = 1, ST_EOS = 2, ST_EVOVERFLOW = 4 };
+enum { ST_NONFINITE = 1, ST_EOS = 2, ST_EVOVERFLOW = 4, ST_TIMEOUT = 8 };
 
 // Budget reduction: [max rho1, sum rho1, sum rho2, sum C_k (MAXS), sum V_D, sum V_F].
 constexpr int NBUD = 5 + MAXS;
@@ -61,7 +68,7 @@ template <class R>
 struct DevParamsR {
   R tau[2], inv_tau[2], G11, G12, G21, a0, inv_rho10, inv_rho20, w_adh[2];
   R eos_a, eos_b4, eos_RT, six_over_G11;
-  R gx, gy, shift_f[2], rho_fill[2];
+  R gx, gy, shift_f[2], shift_fg[2], rho_fill[2];
   R J0[MAXS], Ja[MAXS], inv_tau_g[MAXS], shift_c[MAXS], conc_in[MAXS], cR1[MAXS], cR3[MAXS];
   R k1, k1_inv_Keq, k3, k2, k4, C_F_sat, gas_yield, inv_M_C, c_total_per_rho1;
 };
@@ -74,7 +81,8 @@ struct DevParams {
   double tau[2], G11, G12, G21, a0, rho10, rho20, w_adh[2];
   double eos_a, eos_b, eos_R, eos_T;
   double gx, gy;
-  double shift_f[2];       // population shift rho_ref (0 in FP64 storage)
+  double shift_f[2];       // population shift of liquid nodes, rho_ref (0 in FP64 storage)
+  double shift_fg[2];      // population shift of gas nodes, rho_ref_gas (0 in FP64 storage)
   double rho_fill[2];      // density of a refilled node without fluid neighbours
   double J0[MAXS], tau_g[MAXS], shift_c[MAXS];
   double inv_tau[2], Ja[MAXS], inv_tau_g[MAXS];  // 1/tau, (1 - J0)/4, 1/tau_g
@@ -93,6 +101,11 @@ template <> __host__ __device__ __forceinline__ const DevParamsR<float>& rp<floa
 template <> __host__ __device__ __forceinline__ const DevParamsR<double>& rp<double>(const DevParams& P) { return P.rd; }
 
 struct DevInst {
+  // TMA descriptors of the population boxes of the staged bulk kernel, per tile
+  // shape and ping-pong buffer (encoded only when the instance qualifies:
+  // FP32 populations and rows a multiple of 16 bytes; zero otherwise)
+  CUtensorMap tmf[NSHAPES][2];
+  CUtensorMap tmg[NSHAPES][2];
   DevParams P;
   void* f[2];                 // [2][9][N] populations, ping-pong
   void* g[2];                 // [ns][5][N] solute populations, ping-pong
@@ -187,6 +200,16 @@ __host__ __device__ inline double ord_dec(unsigned long long e) {
   return c.d;
 }
 
+// The liquid threshold of the current step in the compute precision, decoded
+// once per step by the amendment kernel (no FP64 arithmetic in the FP32 bulk).
+template <class R> __device__ __forceinline__ R theta_of(const DevInst* Ip);
+template <> __device__ __forceinline__ double theta_of<double>(const DevInst* Ip) {
+  return __longlong_as_double((long long)Ip->scal[S_THETA]);
+}
+template <> __device__ __forceinline__ float theta_of<float>(const DevInst* Ip) {
+  return __int_as_float((int)(unsigned)Ip->scal[S_THETAF]);
+}
+
 // Eq. 9a with the population shift: delta rho summed in direction order.
 template <class R, class TF>
 __device__ __forceinline__ R density_shifted(const TF* f, long long N, long long node) {
@@ -233,6 +256,13 @@ __device__ __forceinline__ void reservoir_rho(const DevParams& P, uint8_t t, uns
   }
 }
 
+// Population shift of a node of type t: the reference density of its phase
+// (gas-marked nodes: the gas reference; every other type: the liquid one).
+template <class R>
+__device__ __forceinline__ R fshift(const DevParams& P, int comp, uint8_t t) {
+  return (t & T_MASK) == T_GAS ? rp<R>(P).shift_fg[comp] : rp<R>(P).shift_f[comp];
+}
+
 // Marking of an arbitrary node from global memory (same arithmetic as the
 // shared-memory path, so both give the same answer bit for bit).
 template <class R, class TF>
@@ -240,7 +270,7 @@ __device__ __forceinline__ bool liquid_at(const DevParams& P, const uint8_t* tin
                                           R theta) {
   uint8_t t = tin[node] & T_MASK;
   if (!is_fluid(t)) return false;
-  R rho1 = rp<R>(P).shift_f[0] + density_shifted<R>(fin, (long long)N, node);
+  R rho1 = fshift<R>(P, 0, t) + density_shifted<R>(fin, (long long)N, node);
   return rho1 > theta;
 }
 
@@ -271,6 +301,12 @@ template <> __device__ __forceinline__ float rmax<float>(float a, float b) { ret
 template <class R> __device__ __forceinline__ R rexp(R v);
 template <> __device__ __forceinline__ double rexp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float rexp<float>(float v) { return expf(v); }
+// exp(v) - 1 without the cancellation of evaluating exp(v) first (phi_1 of
+// Eq. 15a at the small rho_2 of the liquid phase would lose most of its FP32
+// digits otherwise)
+template <class R> __device__ __forceinline__ R rexpm1(R v);
+template <> __device__ __forceinline__ double rexpm1<double>(double v) { return expm1(v); }
+template <> __device__ __forceinline__ float rexpm1<float>(float v) { return expm1f(v); }
 template <class R> __device__ __forceinline__ R rsqrt_(R v);
 template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return sqrt(v); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqrtf(v); }
@@ -290,7 +326,7 @@ __device__ __forceinline__ void potentials(const DevParams& P, R rho1, R rho2, R
   } else {
     psi = R(0);
   }
-  phi1 = R(1) - rexp<R>(-rho2 * Q.inv_rho20);
+  phi1 = -rexpm1<R>(-rho2 * Q.inv_rho20);
   phi2 = Q.a0 - rexp<R>(-rho1 * Q.inv_rho10);
 }
 
@@ -312,7 +348,7 @@ __device__ __forceinline__ void potentials_q(const DevParamsR<R>& Q, bool has_G1
   } else {
     psi = R(0);
   }
-  phi1 = R(1) - rexp<R>(-rho2 * Q.inv_rho20);
+  phi1 = -rexpm1<R>(-rho2 * Q.inv_rho20);
   phi2 = Q.a0 - rexp<R>(-rho1 * Q.inv_rho10);
 }
 

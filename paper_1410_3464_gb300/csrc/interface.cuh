@@ -128,9 +128,14 @@ __global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles
 __device__ __forceinline__ bool surv_fluid(uint8_t tf) { return (tf & (T_NEW | T_VANISH)) == 0 && is_fluid(tf & T_MASK); }
 __device__ __forceinline__ bool surv_liquid(uint8_t tf) { return tf == T_LIQUID; }
 
-// End of a step for one instance: advance the step counter and free the
-// threshold slot the bulk kernel read (it receives the maximum two steps later).
+// End of a step for one instance: decode the next step's liquid threshold
+// (half the maximum the bulk kernel gathered this step) into both precisions,
+// free the slot this step read (it receives the maximum two steps later) and
+// advance the step counter.
 __device__ __forceinline__ void finish_step(const DevInst* Ip, unsigned long long step) {
+  const double th = 0.5 * ord_dec(Ip->scal[S_MAX0 + int((step + 1) & 1ULL)]);
+  Ip->scal[S_THETA] = (unsigned long long)__double_as_longlong(th);
+  Ip->scal[S_THETAF] = (unsigned long long)(unsigned)__float_as_int(float(th));
   Ip->scal[S_MAX0 + int(step & 1ULL)] = 0ULL;
   Ip->scal[S_NEVENT] = 0ULL;
   Ip->scal[S_STEP] = step + 1;
@@ -213,8 +218,8 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
       const long long nn = (long long)yn * P.nx + xn;
       const uint8_t tf = T[nn];
       if (surv_fluid(tf)) {
-        s1 += rp<R>(P).shift_f[0] + density_c<R>(F, N, nn);
-        s2 += rp<R>(P).shift_f[1] + density_c<R>(F + 9 * N, N, nn);
+        s1 += fshift<R>(P, 0, tf) + density_c<R>(F, N, nn);
+        s2 += fshift<R>(P, 1, tf) + density_c<R>(F + 9 * N, N, nn);
         ++nf;
       }
       if (surv_liquid(tf)) {
@@ -279,8 +284,8 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
         nf += surv_fluid(tz) ? 1 : 0;
         nl += surv_liquid(tz) ? 1 : 0;
       }
-      add1 += (rp<R>(P).shift_f[0] + density_c<R>(F, N, w)) / R(nf);
-      add2 += (rp<R>(P).shift_f[1] + density_c<R>(F + 9 * N, N, w)) / R(nf);
+      add1 += (fshift<R>(P, 0, T[w]) + density_c<R>(F, N, w)) / R(nf);
+      add2 += (fshift<R>(P, 1, T[w]) + density_c<R>(F + 9 * N, N, w)) / R(nf);
       if (nliq && nl) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) {

@@ -28,6 +28,23 @@ void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts)
   if (ntiles <= 0) return;
   k_bulk<SH, KTF, KTG, KR, NS><<<bulk_grid<SH, NS>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
 }
+// Staged variant: grid of as many blocks as fit (two per SM with the
+// double-buffered stage), dynamic shared memory opted in once.
+template <class SH, int SHAPE, int NS>
+void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
+  if (ntiles <= 0) return;
+  using C = StageCfg<SH, KTG, NS>;
+  static int cap = 0;
+  if (cap == 0) {
+    cudaFuncSetAttribute(k_bulk_tma<SH, SHAPE, KTG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk_tma<SH, SHAPE, KTG, NS>, NTHREADS, C::SMEM);
+    cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  k_bulk_tma<SH, SHAPE, KTG, NS><<<ntiles < cap ? ntiles : cap, NTHREADS, C::SMEM, s>>>(tiles, ntiles, insts);
+}
 template <class SH, int NS>
 void vop_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
   if (ntiles <= 0) return;
@@ -55,12 +72,21 @@ void fields_l(cudaStream_t s, const DevInst* I, long long N, double* r1, double*
 template <int NS>
 void budget_l(cudaStream_t s, const DevInst* I, double* part, double* out) {
   k_budget_partial<KTF, KTG, KR, NS><<<BUD_BLOCKS, BUD_THREADS, 0, s>>>(I, part);
-  k_budget_final<<<1, 32, 0, s>>>(part, BUD_BLOCKS, out);
+  k_budget_final<<<1, BUD_FINAL_THREADS, 0, s>>>(part, BUD_BLOCKS, out);
 }
 
 template <int NS>
 constexpr Launchers make() {
-  return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>}, {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>}, &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
+  if constexpr (sizeof(KTF) == 4) {
+    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>},
+                     {&bulk_tma_l<ShapeA, 0, NS>, &bulk_tma_l<ShapeB, 1, NS>},
+                     {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>},
+                     &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
+  } else {
+    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>}, {nullptr, nullptr},
+                     {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>},
+                     &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
+  }
 }
 const Launchers table[MAXS + 1] = {make<0>(), make<1>(), make<2>(), make<3>(), make<4>()};
 

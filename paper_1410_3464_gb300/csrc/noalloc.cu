@@ -38,15 +38,12 @@ double* g_partials_ptr[MAX_DEVICES] = {};
 // Final pass: fixed-order sum of the partial rows into the caller's buffer, in
 // the layout of the PSLBM_F_BUDGET field (max rho1, sum rho1, sum rho2, sum C_k,
 // sum V_D, sum V_F, step count).
-__global__ void k_noalloc_final(const double* __restrict__ part, int nblocks, int ns,
-                                const DevInst* __restrict__ Ip, double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(BUD_FINAL_THREADS) k_noalloc_final(const double* __restrict__ part, int nblocks,
+                                                                     int ns, const DevInst* __restrict__ Ip,
+                                                                     double* __restrict__ out) {
   double v[NBUD];
-  for (int i = 0; i < NBUD; ++i) {
-    double s = (i == 0) ? -1.0 / 0.0 : 0.0;
-    for (int b = 0; b < nblocks; ++b) s = (i == 0) ? fmax(s, part[b * NBUD + i]) : s + part[b * NBUD + i];
-    v[i] = s;
-  }
+  budget_reduce(part, nblocks, v);
+  if (threadIdx.x != 0) return;
   out[0] = v[0] > -1.0 / 0.0 ? v[0] : 0.0;
   out[1] = v[1];
   out[2] = v[2];
@@ -127,7 +124,7 @@ extern "C" pslbm_status pslbm_budget_device_noalloc(pslbm_t h, double* out) {
     case PSLBM_FP32_SOLUTE_BF16: ok = dispatch_ns<float, __nv_bfloat16, float>(ns, s, nblocks, I, part); break;
   }
   if (!ok) return handle_fail(h, PSLBM_ERR_PARAM, "no budget kernel for this precision / species count");
-  k_noalloc_final<<<1, 32, 0, s>>>(part, nblocks, ns, I, out);
+  k_noalloc_final<<<1, BUD_FINAL_THREADS, 0, s>>>(part, nblocks, ns, I, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return handle_fail(h, PSLBM_ERR_CUDA, std::string("budget launch: ") + cudaGetErrorString(e));
   return PSLBM_OK;

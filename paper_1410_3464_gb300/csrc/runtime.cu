@@ -43,7 +43,8 @@ struct GraphCache {
 };
 
 // Launch state shared by a single simulation and a batch: one tile list per
-// tile shape (built on demand), the chosen shape, and the captured graphs.
+// tile shape (built on demand), the chosen bulk-kernel variant (tile shape and
+// staging: plain loads or TMA-staged), and the captured graphs.
 struct Stepper {
   const Launchers* L = nullptr;
   DevInst* d = nullptr;
@@ -52,9 +53,13 @@ struct Stepper {
   Tile* tiles[NSHAPES] = {};
   int ntiles[NSHAPES] = {};
   int shape = 0;
-  bool tuned = false;                      // shape chosen (by timing or by the caller)
+  int staged = 0;                          // 1: TMA-staged bulk kernel
+  int fix_shape = -1;                      // caller's choice, -1: choose by timing
+  int fix_staged = -1;
+  bool staged_ok = false;                  // every instance has TMA descriptors
+  bool tuned = false;                      // variant chosen (by timing or by the caller)
   GraphCache graphs;
-  double trial_ms[NSHAPES] = {};
+  double trial_ms[NSHAPES][2] = {};
   void release() {
     graphs.clear();
     for (int s = 0; s < NSHAPES; ++s) {
@@ -99,7 +104,8 @@ namespace {
 pslbm_status fail(pslbm_t h, pslbm_status s, const std::string& msg) {
   if (h) {
     h->err = msg;
-    if (s == PSLBM_ERR_CUDA || s == PSLBM_ERR_NONFINITE || s == PSLBM_ERR_EOS_DOMAIN) h->sticky = s;
+    if (s == PSLBM_ERR_CUDA || s == PSLBM_ERR_NONFINITE || s == PSLBM_ERR_EOS_DOMAIN || s == PSLBM_ERR_TIMEOUT)
+      h->sticky = s;
   } else {
     std::lock_guard<std::mutex> lk(g_mu);
     g_lib_err = msg;
@@ -177,6 +183,7 @@ void fill_r(DevParamsR<R>& q, const DevParams& P) {
     q.inv_tau[s] = R(P.inv_tau[s]);
     q.w_adh[s] = R(P.w_adh[s]);
     q.shift_f[s] = R(P.shift_f[s]);
+    q.shift_fg[s] = R(P.shift_fg[s]);
     q.rho_fill[s] = R(P.rho_fill[s]);
   }
   q.G11 = R(P.G11);
@@ -229,6 +236,7 @@ DevParams to_dev(const pslbm_params* p) {
     P.tau[s] = p->tau[s];
     P.w_adh[s] = p->w_adh[s];
     P.shift_f[s] = p->precision == PSLBM_FP64 ? 0.0 : p->rho_ref[s];
+    P.shift_fg[s] = p->precision == PSLBM_FP64 ? 0.0 : p->rho_ref_gas[s];
     P.rho_fill[s] = p->rho_ref[s];
     P.rho_in_liq[s] = p->rho_in_liq[s];
     P.rho_in_gas[s] = p->rho_in_gas[s];
@@ -332,19 +340,50 @@ void free_all(pslbm_t h) {
   h->allocs.clear();
 }
 
-// Enqueue n steps of the kernels over the tile list of one shape.
-void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int64_t n) {
+// Enqueue n steps of the kernels for one bulk-kernel variant.
+void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int staged, int64_t n) {
+  auto bulk = staged ? st.L->bulk_tma[shape] : st.L->bulk[shape];
   for (int64_t i = 0; i < n; ++i) {
-    st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
+    bulk(s, st.tiles[shape], st.ntiles[shape], st.d);
     st.L->vop[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
     st.L->amend(s, st.ninst, st.d);
   }
 }
 
-// Tile-shape autotuning: the results do not depend on the shape (the per-node
-// arithmetic and the fixed-order gathers are the same), so the first steps of a
-// run are spent timing each shape (one untimed step, then TUNE_STEPS timed
-// steps per shape) and the fastest is kept.
+// Variants the stepper may use: every tile shape and staging the caller left
+// open (staging only where every instance has TMA descriptors).
+std::vector<std::pair<int, int>> candidates(const Stepper& st) {
+  std::vector<std::pair<int, int>> c;
+  for (int sh = 0; sh < NSHAPES; ++sh) {
+    if (st.fix_shape >= 0 && sh != st.fix_shape) continue;
+    for (int sg = 0; sg < 2; ++sg) {
+      if (st.fix_staged >= 0 && sg != st.fix_staged) continue;
+      if (sg == 1 && !st.staged_ok) continue;
+      c.push_back({sh, sg});
+    }
+  }
+  return c;
+}
+
+// After a change of the caller's choices: a single candidate is taken at once;
+// otherwise the variant is chosen by timing on the next long step call (until
+// then the first candidate runs).
+void choose(Stepper& st) {
+  std::vector<std::pair<int, int>> c = candidates(st);
+  int sh = c.empty() ? 0 : c[0].first, sg = c.empty() ? 0 : c[0].second;
+  // without timing, prefer the staged kernel where it may run
+  for (auto& v : c)
+    if (v.second == 1 && v.first == sh) sg = 1;
+  if (sh != st.shape || sg != st.staged) st.graphs.clear();
+  st.shape = sh;
+  st.staged = sg;
+  st.tuned = c.size() <= 1;
+}
+
+// Variant autotuning: the results do not depend on the variant (the per-node
+// arithmetic and the fixed-order gathers are the same), so the first steps of
+// a run are spent timing each candidate (one untimed step, then TUNE_STEPS
+// timed steps each) and the fastest is kept.
 constexpr int TUNE_STEPS = 3;
 pslbm_status autotune(Stepper& st, std::string& err) {
   cudaStream_t s = lib_stream();
@@ -353,16 +392,19 @@ pslbm_status autotune(Stepper& st, std::string& err) {
     err = "cudaEventCreate failed";
     return PSLBM_ERR_CUDA;
   }
-  int best = 0;
-  for (int sh = 0; sh < NSHAPES; ++sh) {
+  std::vector<std::pair<int, int>> c = candidates(st);
+  double best_ms = 0;
+  int best = -1;
+  for (int i = 0; i < (int)c.size(); ++i) {
+    const int sh = c[i].first, sg = c[i].second;
     cudaError_t e = ensure_tiles(st, sh);
     if (e != cudaSuccess) {
       err = std::string("tile list: ") + cudaGetErrorString(e);
       return e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA;
     }
-    enqueue_steps(s, st, sh, 1);
+    enqueue_steps(s, st, sh, sg, 1);
     cudaEventRecord(a, s);
-    enqueue_steps(s, st, sh, TUNE_STEPS);
+    enqueue_steps(s, st, sh, sg, TUNE_STEPS);
     cudaEventRecord(b, s);
     e = cudaEventSynchronize(b);
     if (e != cudaSuccess) {
@@ -371,24 +413,34 @@ pslbm_status autotune(Stepper& st, std::string& err) {
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
-    st.trial_ms[sh] = ms / TUNE_STEPS;
-    if (st.trial_ms[sh] < st.trial_ms[best]) best = sh;
+    st.trial_ms[sh][sg] = ms / TUNE_STEPS;
+    if (best < 0 || st.trial_ms[sh][sg] < best_ms) {
+      best = i;
+      best_ms = st.trial_ms[sh][sg];
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  if (best != st.shape) st.graphs.clear();
-  st.shape = best;
+  if (best >= 0) {
+    if (c[best].first != st.shape || c[best].second != st.staged) st.graphs.clear();
+    st.shape = c[best].first;
+    st.staged = c[best].second;
+  }
   st.tuned = true;
   return PSLBM_OK;
 }
 
+// Steps the autotuner spends (they advance the simulation like any others).
+int64_t tune_cost(const Stepper& st) { return (int64_t)candidates(st).size() * (TUNE_STEPS + 1); }
+
 // Run n steps, replaying captured graphs of up to 32 steps.
 pslbm_status run_steps(Stepper& st, int64_t n, std::string& err) {
   cudaStream_t s = lib_stream();
-  if (!st.tuned && n >= NSHAPES * (TUNE_STEPS + 1) + 1) {
+  if (!st.tuned && n >= tune_cost(st) + 1) {
+    const int64_t spent = tune_cost(st);
     pslbm_status ts = autotune(st, err);
     if (ts != PSLBM_OK) return ts;
-    n -= NSHAPES * (TUNE_STEPS + 1);
+    n -= spent;
   }
   cudaError_t te = ensure_tiles(st, st.shape);
   if (te != cudaSuccess) {
@@ -407,7 +459,7 @@ pslbm_status run_steps(Stepper& st, int64_t n, std::string& err) {
         err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
         return PSLBM_ERR_CUDA;
       }
-      enqueue_steps(s, st, st.shape, k);
+      enqueue_steps(s, st, st.shape, st.staged, k);
       e = cudaStreamEndCapture(s, &g);
       if (e != cudaSuccess) {
         err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
@@ -432,20 +484,82 @@ pslbm_status run_steps(Stepper& st, int64_t n, std::string& err) {
   return PSLBM_OK;
 }
 
-// Fix the tile shape (tx = ty = 0: choose by timing on the next long run).
+// Fix the tile shape (tx = ty = 0: leave it to timing).
 pslbm_status set_shape(Stepper& st, int tx, int ty) {
-  if (tx == 0 && ty == 0) {
-    st.tuned = false;
-    return PSLBM_OK;
-  }
+  int idx = -2;
+  if (tx == 0 && ty == 0) idx = -1;
   for (int sh = 0; sh < NSHAPES; ++sh)
-    if (SHAPE_TX[sh] == tx && SHAPE_TY[sh] == ty) {
-      if (sh != st.shape) st.graphs.clear();
-      st.shape = sh;
-      st.tuned = true;
-      return PSLBM_OK;
+    if (SHAPE_TX[sh] == tx && SHAPE_TY[sh] == ty) idx = sh;
+  if (idx == -2) return PSLBM_ERR_PARAM;
+  st.fix_shape = idx;
+  choose(st);
+  return PSLBM_OK;
+}
+
+// Fix the staging (-1: leave it to timing, 0: plain loads, 1: TMA-staged).
+pslbm_status set_staging(Stepper& st, int mode) {
+  if (mode < -1 || mode > 1 || (mode == 1 && !st.staged_ok)) return PSLBM_ERR_PARAM;
+  st.fix_staged = mode;
+  choose(st);
+  return PSLBM_OK;
+}
+
+// TMA descriptors of an instance's population boxes (FP32 populations only):
+// per tile shape and ping-pong buffer, a 3D map over (x, y, plane) whose box is
+// the tile plus the staged kernel's ring (D2Q9) or the tile itself (D2Q5).
+// Rows must be a multiple of 16 bytes; returns false when the instance does
+// not qualify or the driver lacks the encoder.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)f;
+  }
+  return fn;
+}
+
+bool encode_maps(DevInst& I, const pslbm_params* p) {
+  if (p->precision == PSLBM_FP64) return false;
+  const size_t gs = gsize(p->precision);
+  const uint64_t nx = (uint64_t)p->nx, ny = (uint64_t)p->ny, N = nx * ny;
+  const int ns = p->n_species;
+  if ((nx * 4) % 16 != 0 || (ns > 0 && (nx * gs) % 16 != 0)) return false;
+  EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const CUtensorMapDataType gt = p->precision == PSLBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : p->precision == PSLBM_FP32_SOLUTE_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  for (int sh = 0; sh < NSHAPES; ++sh) {
+    for (int b = 0; b < 2; ++b) {
+      const cuuint64_t fdim[3] = {nx, ny, 18};
+      const cuuint64_t fstr[2] = {nx * 4, N * 4};
+      const cuuint32_t fbox[3] = {(cuuint32_t)(SHAPE_TX[sh] + 2 * STAGE_HALO_X), (cuuint32_t)(SHAPE_TY[sh] + 2), 18};
+      const cuuint32_t one[3] = {1, 1, 1};
+      if (enc(&I.tmf[sh][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, I.f[b], fdim, fstr, fbox, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+      if (ns > 0) {
+        const cuuint64_t gdim[3] = {nx, ny, (cuuint64_t)(5 * ns)};
+        const cuuint64_t gstr[2] = {nx * gs, N * gs};
+        const cuuint32_t gbox[3] = {(cuuint32_t)SHAPE_TX[sh], (cuuint32_t)SHAPE_TY[sh], (cuuint32_t)(5 * ns)};
+        if (enc(&I.tmg[sh][b], gt, 3, I.g[b], gdim, gstr, gbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+          return false;
+      }
     }
-  return PSLBM_ERR_PARAM;
+  }
+  return true;
 }
 
 pslbm_status device_status(pslbm_t h) {
@@ -454,6 +568,7 @@ pslbm_status device_status(pslbm_t h) {
   CK(h, cudaStreamSynchronize(lib_stream()));
   if (st & ST_NONFINITE) return fail(h, PSLBM_ERR_NONFINITE, "non-finite density on the device");
   if (st & ST_EOS) return fail(h, PSLBM_ERR_EOS_DOMAIN, "Eq. 13 square-root argument negative (rho_1 outside the EOS domain)");
+  if (st & ST_TIMEOUT) return fail(h, PSLBM_ERR_TIMEOUT, "a bounded wait for staged populations gave up");
   return PSLBM_OK;
 }
 
@@ -553,6 +668,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       }
     }
+    h->run.staged_ok = L->bulk_tma[0] != nullptr && encode_maps(I, p);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d, &I, sizeof(DevInst), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
       L->init(s, h->d, dmask, dr1, dr2, dc, N);
@@ -588,7 +704,17 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
         std::memcpy(&bits, &b[0], 8);
         enc = (bits & 0x8000000000000000ULL) ? ~bits : (bits | 0x8000000000000000ULL);
       }
-      e = cudaMemcpyAsync(I.scal + S_MAX0, &enc, sizeof enc, cudaMemcpyHostToDevice, s);
+      // the first step's threshold, as the amendment kernel decodes it
+      const double th = 0.5 * ord_dec(enc);
+      const float thf = float(th);
+      unsigned long long slots[3] = {enc, 0, 0};
+      std::memcpy(&slots[1], &th, 8);
+      uint32_t fb;
+      std::memcpy(&fb, &thf, 4);
+      slots[2] = fb;
+      e = cudaMemcpyAsync(I.scal + S_MAX0, &slots[0], sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(I.scal + S_THETA, &slots[1], 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     if (e != cudaSuccess) {
@@ -601,6 +727,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   h->run.d = h->d;
   h->run.ninst = 1;
   h->run.dims.assign(1, {p->nx, p->ny});
+  choose(h->run);
   {
     cudaError_t e = ensure_tiles(h->run, h->run.shape);
     if (e != cudaSuccess) {
@@ -648,7 +775,7 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
   for (int64_t i = 0; i < n && st == PSLBM_OK; ++i) {
     const int sh = h->run.shape;
     cudaEventRecord(ev[0], s);
-    h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
+    (h->run.staged ? h->L->bulk_tma[sh] : h->L->bulk[sh])(s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[1], s);
     h->L->vop[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[2], s);
@@ -709,6 +836,20 @@ pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, i
   if (tile_x) *tile_x = SHAPE_TX[h->run.shape];
   if (tile_y) *tile_y = SHAPE_TY[h->run.shape];
   if (tuned) *tuned = h->run.tuned ? 1 : 0;
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_set_staging(pslbm_t h, int32_t mode) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (set_staging(h->run, mode) != PSLBM_OK)
+    return fail(h, PSLBM_ERR_PARAM, "staging must be -1, 0 or 1 (1 only where the handle has TMA descriptors)");
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_get_staging(pslbm_t h, int32_t* staged, int32_t* available) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (staged) *staged = h->run.staged;
+  if (available) *available = h->run.staged_ok ? 1 : 0;
   return PSLBM_OK;
 }
 
@@ -844,6 +985,8 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
   }
   pslbm_batch_t b = new (std::nothrow) pslbm_batch_s();
   if (!b) return fail(nullptr, PSLBM_ERR_OOM, "host allocation failed");
+  b->run.staged_ok = true;
+  for (int i = 0; i < n; ++i) b->run.staged_ok = b->run.staged_ok && members[i]->run.staged_ok;
   if (set_shape(b->run, tile_x, tile_y) != PSLBM_OK) {
     delete b;
     return fail(nullptr, PSLBM_ERR_PARAM, "unsupported tile shape (0x0, 16x16 or 32x8)");
@@ -895,6 +1038,20 @@ pslbm_status pslbm_batch_get_tile_shape(pslbm_batch_t b, int32_t* tile_x, int32_
   if (tile_x) *tile_x = SHAPE_TX[b->run.shape];
   if (tile_y) *tile_y = SHAPE_TY[b->run.shape];
   if (tuned) *tuned = b->run.tuned ? 1 : 0;
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_batch_set_staging(pslbm_batch_t b, int32_t mode) {
+  if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
+  if (set_staging(b->run, mode) != PSLBM_OK)
+    return fail(nullptr, PSLBM_ERR_PARAM, "staging must be -1, 0 or 1 (1 only where every member has TMA descriptors)");
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_batch_get_staging(pslbm_batch_t b, int32_t* staged, int32_t* available) {
+  if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
+  if (staged) *staged = b->run.staged;
+  if (available) *available = b->run.staged_ok ? 1 : 0;
   return PSLBM_OK;
 }
 

@@ -53,7 +53,7 @@ def base_params(nx, ny):
         tau=(1.0, 1.0), G11=-1.0, G12=0.001, G21=0.001,
         a0=0.005, rho10=-0.008 / math.log(0.005), rho20=0.003,
         w_adh=(0.0, 0.0), eos_a=1.0, eos_b=4.0, eos_R=1.0, eos_T=0.7 * CS_ORIGINAL["Tc"],
-        body_force=(0.0, 0.0), rho_ref=(1.0, 1.0),
+        body_force=(0.0, 0.0), rho_ref=(1.0, 1.0), rho_ref_gas=(0.0, 0.0),
         n_species=0, idx_A=IDX_ABSENT, idx_B=IDX_ABSENT, idx_E=IDX_ABSENT, idx_F=IDX_ABSENT,
         J0=(0.0,) * MAX_SPECIES, tau_g=(1.0,) * MAX_SPECIES, conc_ref=(0.0,) * MAX_SPECIES,
         k1=0.0, inv_Keq=0.0, k3=0.0, k2=0.0, k4=0.0, C_F_sat=0.0,
@@ -92,7 +92,7 @@ def bubble_grain(nx=128, ny=64, grain=(64, 32, 12), bubble=(24, 32, 10),
     rho1 = np.where(mask == GAS, rg, rl).astype(np.float64)
     rho2 = np.where(mask == GAS, rho2_gas, rho2_liq).astype(np.float64)
     p = base_params(nx, ny)
-    p.update(periodic_x=1, periodic_y=0, rho_ref=(rl, rho2_liq),
+    p.update(periodic_x=1, periodic_y=0, rho_ref=(rl, rho2_liq), rho_ref_gas=(rg, rho2_gas),
              n_species=2, idx_A=0, idx_B=1,
              J0=_pad([1.0 / 3.0, 1.0 / 3.0]), tau_g=_pad([0.8, 0.8], 1.0),
              conc_ref=_pad([1.0, 0.0]),
@@ -207,7 +207,7 @@ def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
     rho1 = np.where(fluid, rl + (rg - rl) * prof, 0.0)
     rho2 = np.where(fluid, rho2_liq + (rho2_gas - rho2_liq) * prof, 0.0)
     p = base_params(nx, ny)
-    p.update(periodic_x=0, periodic_y=0, rho_ref=(rl, rho2_liq),
+    p.update(periodic_x=0, periodic_y=0, rho_ref=(rl, rho2_liq), rho_ref_gas=(rg, rho2_gas),
              n_species=3, idx_A=IDX_DERIVED, idx_B=0, idx_E=1, idx_F=2,
              J0=_pad([1.0 / 3.0] * 3), tau_g=_pad([0.8] * 3, 1.0), conc_ref=_pad([0.0] * 3),
              k1=k1, k3=k3, k2=k2, k4=k4, C_F_sat=0.0,

@@ -29,7 +29,8 @@ EXPORTS = ["pslbm_get_stream", "pslbm_set_stream", "pslbm_create", "pslbm_step",
            "pslbm_budget_device_noalloc", "pslbm_set_step_limit", "pslbm_estimate_device_bytes",
            "pslbm_server_create", "pslbm_server_submit", "pslbm_server_advance", "pslbm_server_poll",
            "pslbm_server_fetch", "pslbm_server_release", "pslbm_server_last_error", "pslbm_server_destroy",
-           "pslbm_set_tile_shape", "pslbm_get_tile_shape", "pslbm_batch_get_tile_shape"]
+           "pslbm_set_tile_shape", "pslbm_get_tile_shape", "pslbm_batch_get_tile_shape",
+           "pslbm_set_staging", "pslbm_get_staging", "pslbm_batch_set_staging", "pslbm_batch_get_staging"]
 
 _D2 = C.c_double * 2
 _DS = C.c_double * MAX_SPECIES
@@ -53,7 +54,7 @@ class Params(C.Structure):
         ("Vbar_D", C.c_double), ("Vbar_F", C.c_double), ("V_split", C.c_double), ("seed", C.c_uint64),
         ("rho_in_liq", _D2), ("rho_in_gas", _D2), ("rho_out", _D2), ("rho_out_gas", _D2),
         ("inlet_period_liq", C.c_int32), ("inlet_period_gas", C.c_int32), ("inlet_ramp", C.c_int32),
-        ("conc_in", _DS),
+        ("conc_in", _DS), ("rho_ref_gas", _D2),
     ]
 
 
@@ -137,6 +138,10 @@ def load():
     lib.pslbm_set_tile_shape.argtypes = [vp, i32, i32]
     lib.pslbm_get_tile_shape.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.pslbm_batch_get_tile_shape.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    lib.pslbm_set_staging.argtypes = [vp, i32]
+    lib.pslbm_get_staging.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    lib.pslbm_batch_set_staging.argtypes = [vp, i32]
+    lib.pslbm_batch_get_staging.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("pslbm_get_stream", "pslbm_last_error", "pslbm_server_last_error"):
@@ -207,6 +212,16 @@ class Simulation:
         tx, ty, tu = C.c_int32(), C.c_int32(), C.c_int32()
         _check(load().pslbm_get_tile_shape(self.h, C.byref(tx), C.byref(ty), C.byref(tu)), self.h)
         return tx.value, ty.value, bool(tu.value)
+
+    def set_staging(self, mode):
+        """-1: choose by timing, 0: plain-load bulk kernel, 1: TMA-staged."""
+        _check(load().pslbm_set_staging(self.h, int(mode)), self.h)
+
+    def staging(self):
+        """(staged kernel in use, staged kernel available) as booleans."""
+        sg, av = C.c_int32(), C.c_int32()
+        _check(load().pslbm_get_staging(self.h, C.byref(sg), C.byref(av)), self.h)
+        return bool(sg.value), bool(av.value)
 
     def set_step_limit(self, limit):
         _check(load().pslbm_set_step_limit(self.h, int(limit)), self.h)
@@ -291,6 +306,14 @@ class Batch:
         tx, ty, tu = C.c_int32(), C.c_int32(), C.c_int32()
         _check(load().pslbm_batch_get_tile_shape(self.b, C.byref(tx), C.byref(ty), C.byref(tu)))
         return tx.value, ty.value, bool(tu.value)
+
+    def set_staging(self, mode):
+        _check(load().pslbm_batch_set_staging(self.b, int(mode)))
+
+    def staging(self):
+        sg, av = C.c_int32(), C.c_int32()
+        _check(load().pslbm_batch_get_staging(self.b, C.byref(sg), C.byref(av)))
+        return bool(sg.value), bool(av.value)
 
     def close(self):
         if getattr(self, "b", None):
