@@ -190,12 +190,13 @@ pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes)
 pslbm_status pslbm_set_tile_shape(pslbm_t h, int32_t tile_x, int32_t tile_y);
 pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, int32_t* tuned);
 
-/* Staging of the bulk kernel's populations: 0 plain per-thread loads, 1 TMA
+/* Staging of the bulk kernel's populations: 0 plain per-thread loads; 1 TMA
  * copies of each tile's population box into shared memory two tiles ahead
- * (available for the FP32-population precisions when a row of the lattice is a
- * multiple of 16 bytes: nx a multiple of 4, and of 8 with 16-bit solutes),
- * -1 (the default) leaves it to timing.  PSLBM_ERR_PARAM for 1 where it is not
- * available.  The results are bit-identical either way.  get reports the
+ * (two stages, two blocks per SM); 2 the same one tile ahead (one stage, three
+ * blocks per SM).  1 and 2 are available for the FP32-population precisions
+ * when a row of the lattice is a multiple of 16 bytes (nx a multiple of 4, and
+ * of 8 with 16-bit solutes).  -1 (the default) leaves the choice to timing.
+ * PSLBM_ERR_PARAM for 1 or 2 where they are not available.  The results are bit-identical either way.  get reports the
  * staging in use and whether staging is available for the handle.  A staged
  * kernel whose copy does not arrive within about a second stops and sets
  * PSLBM_ERR_TIMEOUT (sticky), reported by the next sync or read. */

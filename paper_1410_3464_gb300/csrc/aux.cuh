@@ -100,23 +100,26 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
           sv = R(0);
         }
         const R w = wf<R>(a);
-        // differences from the centre value, as in the bulk kernel
-        const R vp = w * (ps - psc), v2 = w * (q2 - p2c), v1 = w * (q1 - p1c), vs = w * sv;
-        if (EX(a) > 0) { spx += vp; s2x += v2; s1x += v1; ssx += vs; }
-        if (EX(a) < 0) { spx -= vp; s2x -= v2; s1x -= v1; ssx -= vs; }
-        if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
-        if (EY(a) < 0) { spy -= vp; s2y -= v2; s1y -= v1; ssy -= vs; }
+        // differences from the centre value, in the bulk kernels' operation order
+        const R vp = sv == R(0) ? rmul<R>(w, rsub<R>(ps, psc)) : R(0);
+        const R v2 = sv == R(0) ? rmul<R>(w, rsub<R>(q2, p2c)) : R(0);
+        const R v1 = sv == R(0) ? rmul<R>(w, rsub<R>(q1, p1c)) : R(0);
+        const R vs = rmul<R>(w, sv);
+        stencil_acc<R>(spx, vp, EX(a)); stencil_acc<R>(s2x, v2, EX(a));
+        stencil_acc<R>(s1x, v1, EX(a)); stencil_acc<R>(ssx, vs, EX(a));
+        stencil_acc<R>(spy, vp, EY(a)); stencil_acc<R>(s2y, v2, EY(a));
+        stencil_acc<R>(s1y, v1, EY(a)); stencil_acc<R>(ssy, vs, EY(a));
       }
       const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0], w2 = rp<R>(P).w_adh[1];
-      const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * rp<R>(P).gx;
-      const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * rp<R>(P).gy;
-      const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * rp<R>(P).gx;
-      const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * rp<R>(P).gy;
-      const R rt = rho1 + rho2;
+      const R F1x = force1<R>(G11, G12, w1, psc, p1c, spx, s2x, ssx, rho1, rp<R>(P).gx);
+      const R F1y = force1<R>(G11, G12, w1, psc, p1c, spy, s2y, ssy, rho1, rp<R>(P).gy);
+      const R F2x = force2<R>(G21, w2, p2c, s1x, ssx, rho2, rp<R>(P).gx);
+      const R F2y = force2<R>(G21, w2, p2c, s1y, ssy, rho2, rp<R>(P).gy);
+      const R rrt = rrcp<R>(radd<R>(rho1, rho2));
       r1o = double(rho1);
       r2o = double(rho2);
-      uxo = double((j1x + j2x + R(0.5) * (F1x + F2x)) / rt);
-      uyo = double((j1y + j2y + R(0.5) * (F1y + F2y)) / rt);
+      uxo = double(u_phys<R>(j1x, j2x, F1x, F2x, rrt));
+      uyo = double(u_phys<R>(j1y, j2y, F1y, F2y, rrt));
     }
     if (o_rho1) o_rho1[node] = r1o;
     if (o_rho2) o_rho2[node] = r2o;

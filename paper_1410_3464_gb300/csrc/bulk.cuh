@@ -414,33 +414,33 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
       const int en = eo + EY(a) * SH::EXT_X + EX(a);
       const bool lv = is_live(st_[en]);
       const R w = wf<R>(a);
-      const R vp = lv ? w * (sp[en] - psc) : R(0);
-      const R v2 = lv ? w * (sq2[en] - p2c) : R(0);
-      const R v1 = lv ? w * (sq1[en] - p1c) : R(0);
+      const R vp = lv ? rmul<R>(w, rsub<R>(sp[en], psc)) : R(0);
+      const R v2 = lv ? rmul<R>(w, rsub<R>(sq2[en], p2c)) : R(0);
+      const R v1 = lv ? rmul<R>(w, rsub<R>(sq1[en], p1c)) : R(0);
       const R vs = lv ? R(0) : w;
-      if (EX(a) > 0) { spx += vp; s2x += v2; s1x += v1; ssx += vs; }
-      if (EX(a) < 0) { spx -= vp; s2x -= v2; s1x -= v1; ssx -= vs; }
-      if (EY(a) > 0) { spy += vp; s2y += v2; s1y += v1; ssy += vs; }
-      if (EY(a) < 0) { spy -= vp; s2y -= v2; s1y -= v1; ssy -= vs; }
+      stencil_acc<R>(spx, vp, EX(a)); stencil_acc<R>(s2x, v2, EX(a));
+      stencil_acc<R>(s1x, v1, EX(a)); stencil_acc<R>(ssx, vs, EX(a));
+      stencil_acc<R>(spy, vp, EY(a)); stencil_acc<R>(s2y, v2, EY(a));
+      stencil_acc<R>(s1y, v1, EY(a)); stencil_acc<R>(ssy, vs, EY(a));
     }
     const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0],
             w2 = rp<R>(P).w_adh[1];
-    const R F1x = -G11 * psc * spx - G12 * p1c * s2x - w1 * psc * ssx + rho1 * rp<R>(P).gx;
-    const R F1y = -G11 * psc * spy - G12 * p1c * s2y - w1 * psc * ssy + rho1 * rp<R>(P).gy;
-    const R F2x = -G21 * p2c * s1x - w2 * rho2 * ssx + rho2 * rp<R>(P).gx;
-    const R F2y = -G21 * p2c * s1y - w2 * rho2 * ssy + rho2 * rp<R>(P).gy;
+    const R F1x = force1<R>(G11, G12, w1, psc, p1c, spx, s2x, ssx, rho1, rp<R>(P).gx);
+    const R F1y = force1<R>(G11, G12, w1, psc, p1c, spy, s2y, ssy, rho1, rp<R>(P).gy);
+    const R F2x = force2<R>(G21, w2, p2c, s1x, ssx, rho2, rp<R>(P).gx);
+    const R F2y = force2<R>(G21, w2, p2c, s1y, ssy, rho2, rp<R>(P).gy);
     // ---- velocities (Eqs. 17-19)
     const R it1 = rp<R>(P).inv_tau[0], it2 = rp<R>(P).inv_tau[1];
-    const R rden = rrcp<R>(rho1 * it1 + rho2 * it2);
-    const R upx = (j1x * it1 + j2x * it2) * rden;
-    const R upy = (j1y * it1 + j2y * it2) * rden;
-    const R q1 = rho1 != R(0) ? rp<R>(P).tau[0] * rrcp<R>(rho1) : R(0);
-    const R q2 = rho2 != R(0) ? rp<R>(P).tau[1] * rrcp<R>(rho2) : R(0);
-    const R u1x = upx + F1x * q1, u1y = upy + F1y * q1;
-    const R u2x = upx + F2x * q2, u2y = upy + F2y * q2;
-    const R rrt = rrcp<R>(rho1 + rho2);
-    const R urx = (j1x + j2x + R(0.5) * (F1x + F2x)) * rrt;
-    const R ury = (j1y + j2y + R(0.5) * (F1y + F2y)) * rrt;
+    const R rden = rrcp<R>(rfma<R>(rho1, it1, rmul<R>(rho2, it2)));
+    const R upx = u_common<R>(j1x, j2x, it1, it2, rden);
+    const R upy = u_common<R>(j1y, j2y, it1, it2, rden);
+    const R q1 = rho1 != R(0) ? rmul<R>(rp<R>(P).tau[0], rrcp<R>(rho1)) : R(0);
+    const R q2 = rho2 != R(0) ? rmul<R>(rp<R>(P).tau[1], rrcp<R>(rho2)) : R(0);
+    const R u1x = rfma<R>(F1x, q1, upx), u1y = rfma<R>(F1y, q1, upy);
+    const R u2x = rfma<R>(F2x, q2, upx), u2y = rfma<R>(F2y, q2, upy);
+    const R rrt = rrcp<R>(radd<R>(rho1, rho2));
+    const R urx = u_phys<R>(j1x, j2x, F1x, F2x, rrt);
+    const R ury = u_phys<R>(j1y, j2y, F1y, F2y, rrt);
 
     const bool liq = sm_[eo] != 0;
     tout[node] = liq ? T_LIQUID : T_GAS;
@@ -472,7 +472,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
 #pragma unroll
             for (int a = 0; a < 5; ++a) {
               const R ja = a == 0 ? J0 : Ja;
-              gs[k][a] = appear ? ja * (cb[k] + dC[k]) - ja * rp<R>(P).shift_c[k] : gs[k][a] + ja * dC[k];
+              gs[k][a] = appear ? rfma<R>(ja, radd<R>(cb[k], dC[k]), -rmul<R>(ja, rp<R>(P).shift_c[k]))
+                                : rfma<R>(ja, dC[k], gs[k][a]);
             }
           }
         }
@@ -492,14 +493,16 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
           if (k == P.iE) CE = C[k];
           tot += C[k];
         }
-        if (P.iA == -2) CA = rmax<R>(R(0), rp<R>(P).c_total_per_rho1 * rho1 - tot);
-        R R1 = rp<R>(P).k1 * CA;
-        if (P.has_rev) R1 -= rp<R>(P).k1_inv_Keq * CB * rsqrt_<R>(rmax<R>(rho2 * rp<R>(P).inv_M_C, R(0)));
-        const R R3 = rp<R>(P).k3 * CB * CE;
+        if (P.iA == -2) CA = rmax<R>(R(0), rfma<R>(rp<R>(P).c_total_per_rho1, rho1, -tot));
+        R R1 = rmul<R>(rp<R>(P).k1, CA);
+        if (P.has_rev)
+          R1 = rsub<R>(R1, rmul<R>(rmul<R>(rp<R>(P).k1_inv_Keq, CB),
+                                   rsqrt_<R>(rmax<R>(rmul<R>(rho2, rp<R>(P).inv_M_C), R(0)))));
+        const R R3 = rmul<R>(rmul<R>(rp<R>(P).k3, CB), CE);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) Sk[k] = rp<R>(P).cR1[k] * R1 + rp<R>(P).cR3[k] * R3;
-        S1 = -rp<R>(P).gas_yield * R1;
-        S2 = rp<R>(P).gas_yield * R1;
+        for (int k = 0; k < NS; ++k) Sk[k] = rfma<R>(rp<R>(P).cR1[k], R1, rmul<R>(rp<R>(P).cR3[k], R3));
+        S1 = -rmul<R>(rp<R>(P).gas_yield, R1);
+        S2 = rmul<R>(rp<R>(P).gas_yield, R1);
       }
     }
 
@@ -513,7 +516,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
       const R ux = s == 0 ? u1x : u2x, uy = s == 0 ? u1y : u2y;
       const R itau = s == 0 ? it1 : it2;
       const R Ssrc = s == 0 ? S1 : S2;
-      const R uu = R(1.5) * (ux * ux + uy * uy);
+      const R uu = half_u2<R>(ux, uy);
       const R shs = s == 0 ? sh1 : sh2;
       const R dl = shs - rp<R>(P).shift_f[s], dg = shs - rp<R>(P).shift_fg[s];
       const R down = liq ? dl : dg;
@@ -521,20 +524,20 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         const R fa = s == 0 ? f1[a] : f2[a];
-        const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
+        const R eu = R(EX(a)) * ux + R(EY(a)) * uy;   // exact: e has components 0, +-1
         const R w = w9<R>(a);
-        const R feq = w * (dr + rho * (R(3) * eu + R(4.5) * eu * eu - uu));
-        const R fs = fa - (fa - feq) * itau + w * Ssrc;
+        const R feq = feq_shifted<R>(w, dr, rho, eu, uu);
+        const R fs = bgk<R>(fa, feq, itau, w, Ssrc);
         if (a == 0) {
-          st<TF, R>(fo + node, fs + w * down);
+          st<TF, R>(fo + node, rfma<R>(w, down, fs));
           continue;
         }
         const int en = eo + EY(a) * SH::EXT_X + EX(a);
         const uint8_t tn = st_[en];
         if (is_fluid(tn))
-          st<TF, R>(fo + a * N + nb[a], fs + w * (sm_[en] ? dl : dg));
+          st<TF, R>(fo + a * N + nb[a], rfma<R>(w, sm_[en] ? dl : dg, fs));
         else if (!is_res(tn))
-          st<TF, R>(fo + OPP(a) * N + node, fs + w * down);
+          st<TF, R>(fo + OPP(a) * N + node, rfma<R>(w, down, fs));
       }
     }
 
@@ -561,8 +564,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
             const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
-            const R geq = ja * (C[k] - rp<R>(P).shift_c[k]) + R(0.5) * C[k] * eu;
-            const R gst = gs[k][a] - (gs[k][a] - geq) * rp<R>(P).inv_tau_g[k] + ja * Sk[k];
+            const R geq = geq_shifted<R>(ja, C[k], rp<R>(P).shift_c[k], eu);
+            const R gst = bgk<R>(gs[k][a], geq, rp<R>(P).inv_tau_g[k], ja, Sk[k]);
             if (keep) st<TG, R>(gout + (k * 5 + slot) * N + dst, gst);
           }
         }
@@ -638,7 +641,6 @@ struct StageCfg {
   static constexpr int FOFF = 0;
   static constexpr int GOFF = ((FBYTES + 127) / 128) * 128;
   static constexpr int STAGE = GOFF + ((GBYTES + 127) / 128) * 128;
-  static constexpr int SMEM = 2 * STAGE;
   static constexpr uint32_t TX_BYTES = FBYTES + GBYTES;
 };
 
@@ -713,13 +715,19 @@ __device__ __forceinline__ void stage_issue(const Tile* tiles, const DevInst* in
   if constexpr (NS > 0) tma_load_3d(stage + C::GOFF, mg, bar, tl.x0, tl.y0, 0);
 }
 
-// Staged bulk kernel (FP32 populations): while the block computes tile j, the
-// TMA unit brings tiles j+1 and j+2 into the two shared stages, so the
-// populations' DRAM latency overlaps arithmetic instead of stalling it.  The
-// arithmetic is the plain kernel's, value for value.
-template <class SH, int SHAPE, class TG, int NS>
-__global__ void __launch_bounds__(NTHREADS, 2) k_bulk_tma(const Tile* __restrict__ tiles, int ntiles,
-                                                          const DevInst* __restrict__ insts) {
+// Staged bulk kernel (FP32 populations): the TMA unit brings each tile's
+// population box into shared memory ahead of its use, so the populations'
+// DRAM latency overlaps arithmetic instead of stalling it.  A tile reads its
+// stage only before the tile's barrier (into registers), so the stage can be
+// refilled right after it.  STAGES = 2: two stages, the copy of tile j+2 is
+// issued at tile j's barrier (two blocks per SM fit); STAGES = 1: one stage,
+// the copy of tile j+1 is issued at tile j's barrier (half the shared memory,
+// three blocks per SM).  The arithmetic is the plain kernel's, value for
+// value.
+template <class SH, int SHAPE, class TG, int NS, int STAGES>
+__global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3) k_bulk_tma(const Tile* __restrict__ tiles,
+                                                                            int ntiles,
+                                                                            const DevInst* __restrict__ insts) {
   using C = StageCfg<SH, TG, NS>;
   using R = float;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -738,14 +746,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_bulk_tma(const Tile* __restrict
   __syncthreads();
   if (threadIdx.x == 0) {
     if (ti < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, ti, dyn, &bars[0]);
-    if (t1 < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, t1, dyn + C::STAGE, &bars[1]);
+    if (STAGES == 2 && t1 < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, t1, dyn + C::STAGE, &bars[1]);
   }
   TileTypes tt;
   if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, threadIdx.x);
   int j = 0;                        // tiles processed by this block
   uint32_t phase = 0;               // parity bit per stage
   while (ti < ntiles) {
-    const int b = j & 1;
+    const int b = STAGES == 2 ? (j & 1) : 0;     // stage of this tile
+    const int sb = j & 1;                         // shared buffers of this tile
     const int t2 = t1 < ntiles ? next_live(tiles, ntiles, insts, t1 + stride, stride) : ntiles;
     const bool ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
     phase ^= 1u << b;
@@ -755,18 +764,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_bulk_tma(const Tile* __restrict
     unsigned char* stage = dyn + b * C::STAGE;
     const StageSrc<SH, TG, NS> src{(const float*)(stage + C::FOFF), (const TG*)(stage + C::GOFF),
                                    (const float*)Ip->f[cur], (int)Ip->N, Ip->P.nx, Ip->P.ny, tl.x0, tl.y0};
-    // after the tile's barrier its stage is free: refill it with tile j+2
+    // after the tile's barrier its stage is free: refill it with the next
+    // tile this stage serves
+    const int tn = STAGES == 2 ? t2 : t1;
     auto refill = [&] {
-      if (threadIdx.x == 0 && t2 < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, t2, stage, &bars[b]);
+      if (threadIdx.x == 0 && tn < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, tn, stage, &bars[b]);
     };
-    if (bulk_tile<SH, float, TG, R, NS>(tl, Ip, src, refill, ok, tt, tiles, ntiles, insts, t1, s_psi[b], s_phi1[b],
-                                        s_phi2[b], s_t[b], s_m[b])) {
+    if (bulk_tile<SH, float, TG, R, NS>(tl, Ip, src, refill, ok, tt, tiles, ntiles, insts, t1, s_psi[sb], s_phi1[sb],
+                                        s_phi2[sb], s_t[sb], s_m[sb])) {
       // a wait gave up: record it, let the copies still in flight land
-      // (bounded waits: this tile's stage, and the next tile's), and leave
+      // (bounded waits: this tile's stage, and with two stages the next
+      // tile's), and leave
       if (threadIdx.x == 0) {
         atomicOr(&Ip->scal[S_STATUS], (unsigned long long)ST_TIMEOUT);
         mbar_wait_bounded(&bars[b], ((phase >> b) & 1u) ^ 1u);
-        if (t1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
+        if (STAGES == 2 && t1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
       }
       return;
     }

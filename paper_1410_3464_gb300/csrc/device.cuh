@@ -301,6 +301,71 @@ template <> __device__ __forceinline__ float rmax<float>(float a, float b) { ret
 template <class R> __device__ __forceinline__ R rexp(R v);
 template <> __device__ __forceinline__ double rexp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float rexp<float>(float v) { return expf(v); }
+// Arithmetic helpers of the force, velocity and collision formulas (plain
+// operators: the compiler may fuse a product into a following sum; every bulk
+// kernel variant runs the same tile body, so all variants round identically).
+template <class R> __device__ __forceinline__ R radd(R a, R b) { return a + b; }
+template <class R> __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
+template <class R> __device__ __forceinline__ R rmul(R a, R b) { return a * b; }
+template <class R> __device__ __forceinline__ R rfma(R a, R b, R c) { return a * b + c; }
+
+// One term of the force stencils: accumulate +-w (v_n - v_c) along one axis
+// (dir = +1, -1 or 0; a constant once the direction loop is unrolled).
+template <class R>
+__device__ __forceinline__ void stencil_acc(R& s, R wv, int dir) {
+  if (dir > 0) s = radd<R>(s, wv);
+  if (dir < 0) s = rsub<R>(s, wv);
+}
+
+// F_1 (Eqs. 11, 14a, 16 and the body force) from its stencil sums, and F_2
+// (Eqs. 14b, 16), in a fixed operation order.
+template <class R>
+__device__ __forceinline__ R force1(R G11, R G12, R w1, R psc, R p1c, R sp, R s2, R ss, R rho1, R g) {
+  const R a = rmul<R>(rmul<R>(G11, psc), sp);
+  const R b = rmul<R>(rmul<R>(G12, p1c), s2);
+  const R c = rmul<R>(rmul<R>(w1, psc), ss);
+  return radd<R>(rsub<R>(rsub<R>(-a, b), c), rmul<R>(rho1, g));
+}
+template <class R>
+__device__ __forceinline__ R force2(R G21, R w2, R p2c, R s1, R ss, R rho2, R g) {
+  const R a = rmul<R>(rmul<R>(G21, p2c), s1);
+  const R c = rmul<R>(rmul<R>(w2, rho2), ss);
+  return radd<R>(rsub<R>(-a, c), rmul<R>(rho2, g));
+}
+
+// Common velocity u' (Eq. 18) of one axis, and u_r (Eq. 19).
+template <class R>
+__device__ __forceinline__ R u_common(R j1, R j2, R it1, R it2, R rden) {
+  return rmul<R>(rfma<R>(j1, it1, rmul<R>(j2, it2)), rden);
+}
+template <class R>
+__device__ __forceinline__ R u_phys(R j1, R j2, R F1, R F2, R rrt) {
+  return rmul<R>(rfma<R>(R(0.5), radd<R>(F1, F2), radd<R>(j1, j2)), rrt);
+}
+
+// D2Q9 equilibrium relative to a node's shift (Eq. 8): w (dr + rho (3 eu +
+// 4.5 eu^2 - uu)) with dr = rho - shift and uu = 1.5 |u|^2, and the BGK
+// collision with source (Eq. 6): f - (f - feq) / tau + w S.
+template <class R>
+__device__ __forceinline__ R feq_shifted(R w, R dr, R rho, R eu, R uu) {
+  const R t = rsub<R>(rfma<R>(rmul<R>(R(4.5), eu), eu, rmul<R>(R(3), eu)), uu);
+  return rmul<R>(w, rfma<R>(rho, t, dr));
+}
+template <class R>
+__device__ __forceinline__ R bgk(R fa, R feq, R itau, R w, R S) {
+  return rfma<R>(w, S, rfma<R>(-rsub<R>(fa, feq), itau, fa));
+}
+template <class R>
+__device__ __forceinline__ R half_u2(R ux, R uy) {
+  return rmul<R>(R(1.5), rfma<R>(ux, ux, rmul<R>(uy, uy)));
+}
+// D2Q5 equilibrium relative to the solute shift (Eq. 21) and collision with
+// the homogeneous source (Eq. 20): geq = J (C - shift) + C e.u / 2.
+template <class R>
+__device__ __forceinline__ R geq_shifted(R ja, R C, R sh, R eu) {
+  return rfma<R>(ja, rsub<R>(C, sh), rmul<R>(rmul<R>(R(0.5), C), eu));
+}
+
 // exp(v) - 1 without the cancellation of evaluating exp(v) first (phi_1 of
 // Eq. 15a at the small rho_2 of the liquid phase would lose most of its FP32
 // digits otherwise)

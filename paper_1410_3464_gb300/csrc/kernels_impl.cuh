@@ -28,22 +28,24 @@ void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts)
   if (ntiles <= 0) return;
   k_bulk<SH, KTF, KTG, KR, NS><<<bulk_grid<SH, NS>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
 }
-// Staged variant: grid of as many blocks as fit (two per SM with the
-// double-buffered stage), dynamic shared memory opted in once.
-template <class SH, int SHAPE, int NS>
+// Staged variants: grid of as many blocks as fit (two per SM with the
+// double-buffered stage, three with the single stage), dynamic shared memory
+// opted in once.
+template <class SH, int SHAPE, int NS, int STAGES>
 void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
   if (ntiles <= 0) return;
   using C = StageCfg<SH, KTG, NS>;
+  constexpr int smem = STAGES * C::STAGE;
   static int cap = 0;
   if (cap == 0) {
-    cudaFuncSetAttribute(k_bulk_tma<SH, SHAPE, KTG, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaFuncSetAttribute(k_bulk_tma<SH, SHAPE, KTG, NS, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk_tma<SH, SHAPE, KTG, NS>, NTHREADS, C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk_tma<SH, SHAPE, KTG, NS, STAGES>, NTHREADS, smem);
     cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
-  k_bulk_tma<SH, SHAPE, KTG, NS><<<ntiles < cap ? ntiles : cap, NTHREADS, C::SMEM, s>>>(tiles, ntiles, insts);
+  k_bulk_tma<SH, SHAPE, KTG, NS, STAGES><<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts);
 }
 template <class SH, int NS>
 void vop_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
@@ -79,11 +81,12 @@ template <int NS>
 constexpr Launchers make() {
   if constexpr (sizeof(KTF) == 4) {
     return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>},
-                     {&bulk_tma_l<ShapeA, 0, NS>, &bulk_tma_l<ShapeB, 1, NS>},
+                     {&bulk_tma_l<ShapeA, 0, NS, 2>, &bulk_tma_l<ShapeB, 1, NS, 2>},
+                     {&bulk_tma_l<ShapeA, 0, NS, 1>, &bulk_tma_l<ShapeB, 1, NS, 1>},
                      {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>},
                      &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
   } else {
-    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>}, {nullptr, nullptr},
+    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>}, {nullptr, nullptr}, {nullptr, nullptr},
                      {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>},
                      &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
   }

@@ -9,6 +9,8 @@ struct Launchers {
   void (*bulk[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
   // TMA-staged bulk kernel (FP32 populations only; null for FP64)
   void (*bulk_tma[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
+  // TMA-staged bulk kernel with a single stage and three blocks per SM
+  void (*bulk_tma1[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
   void (*vop[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
   void (*amend)(cudaStream_t, int ninst, const DevInst*);
   void (*init)(cudaStream_t, DevInst*, const uint8_t*, const double*, const double*, const double*, long long N);

@@ -42,6 +42,8 @@ struct GraphCache {
   }
 };
 
+constexpr int NSTAGING = 3;
+
 // Launch state shared by a single simulation and a batch: one tile list per
 // tile shape (built on demand), the chosen bulk-kernel variant (tile shape and
 // staging: plain loads or TMA-staged), and the captured graphs.
@@ -53,13 +55,13 @@ struct Stepper {
   Tile* tiles[NSHAPES] = {};
   int ntiles[NSHAPES] = {};
   int shape = 0;
-  int staged = 0;                          // 1: TMA-staged bulk kernel
+  int staged = 0;                          // 1: TMA-staged, two stages; 2: TMA-staged, one stage
   int fix_shape = -1;                      // caller's choice, -1: choose by timing
   int fix_staged = -1;
   bool staged_ok = false;                  // every instance has TMA descriptors
   bool tuned = false;                      // variant chosen (by timing or by the caller)
   GraphCache graphs;
-  double trial_ms[NSHAPES][2] = {};
+  double trial_ms[NSHAPES][NSTAGING] = {};
   void release() {
     graphs.clear();
     for (int s = 0; s < NSHAPES; ++s) {
@@ -342,7 +344,7 @@ void free_all(pslbm_t h) {
 
 // Enqueue n steps of the kernels for one bulk-kernel variant.
 void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int staged, int64_t n) {
-  auto bulk = staged ? st.L->bulk_tma[shape] : st.L->bulk[shape];
+  auto bulk = staged == 2 ? st.L->bulk_tma1[shape] : staged == 1 ? st.L->bulk_tma[shape] : st.L->bulk[shape];
   for (int64_t i = 0; i < n; ++i) {
     bulk(s, st.tiles[shape], st.ntiles[shape], st.d);
     st.L->vop[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
@@ -356,9 +358,9 @@ std::vector<std::pair<int, int>> candidates(const Stepper& st) {
   std::vector<std::pair<int, int>> c;
   for (int sh = 0; sh < NSHAPES; ++sh) {
     if (st.fix_shape >= 0 && sh != st.fix_shape) continue;
-    for (int sg = 0; sg < 2; ++sg) {
+    for (int sg = 0; sg < NSTAGING; ++sg) {
       if (st.fix_staged >= 0 && sg != st.fix_staged) continue;
-      if (sg == 1 && !st.staged_ok) continue;
+      if (sg >= 1 && !st.staged_ok) continue;
       c.push_back({sh, sg});
     }
   }
@@ -371,9 +373,9 @@ std::vector<std::pair<int, int>> candidates(const Stepper& st) {
 void choose(Stepper& st) {
   std::vector<std::pair<int, int>> c = candidates(st);
   int sh = c.empty() ? 0 : c[0].first, sg = c.empty() ? 0 : c[0].second;
-  // without timing, prefer the staged kernel where it may run
+  // without timing, prefer the most staged kernel that may run
   for (auto& v : c)
-    if (v.second == 1 && v.first == sh) sg = 1;
+    if (v.first == sh && v.second > sg) sg = v.second;
   if (sh != st.shape || sg != st.staged) st.graphs.clear();
   st.shape = sh;
   st.staged = sg;
@@ -496,9 +498,10 @@ pslbm_status set_shape(Stepper& st, int tx, int ty) {
   return PSLBM_OK;
 }
 
-// Fix the staging (-1: leave it to timing, 0: plain loads, 1: TMA-staged).
+// Fix the staging (-1: leave it to timing, 0: plain loads, 1: TMA-staged,
+// 2: TMA-staged with a single stage).
 pslbm_status set_staging(Stepper& st, int mode) {
-  if (mode < -1 || mode > 1 || (mode == 1 && !st.staged_ok)) return PSLBM_ERR_PARAM;
+  if (mode < -1 || mode >= NSTAGING || (mode >= 1 && !st.staged_ok)) return PSLBM_ERR_PARAM;
   st.fix_staged = mode;
   choose(st);
   return PSLBM_OK;
@@ -768,6 +771,10 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
   if (n < 1 || !kernel_ms) return fail(h, PSLBM_ERR_PARAM, "n < 1 or kernel_ms is NULL");
   if (h->in_batch) return fail(h, PSLBM_ERR_STATE, "handle is a member of a batch");
   cudaStream_t s = lib_stream();
+  {
+    cudaError_t te = ensure_tiles(h->run, h->run.shape);
+    if (te != cudaSuccess) return fail(h, PSLBM_ERR_CUDA, std::string("tile list: ") + cudaGetErrorString(te));
+  }
   cudaEvent_t ev[4];
   for (int i = 0; i < 4; ++i) CK(h, cudaEventCreate(&ev[i]));
   double acc[3] = {0, 0, 0}, tot = 0;
@@ -775,7 +782,9 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
   for (int64_t i = 0; i < n && st == PSLBM_OK; ++i) {
     const int sh = h->run.shape;
     cudaEventRecord(ev[0], s);
-    (h->run.staged ? h->L->bulk_tma[sh] : h->L->bulk[sh])(s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
+    (h->run.staged == 2   ? h->L->bulk_tma1[sh]
+     : h->run.staged == 1 ? h->L->bulk_tma[sh]
+                          : h->L->bulk[sh])(s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[1], s);
     h->L->vop[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[2], s);
@@ -842,7 +851,7 @@ pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, i
 pslbm_status pslbm_set_staging(pslbm_t h, int32_t mode) {
   if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
   if (set_staging(h->run, mode) != PSLBM_OK)
-    return fail(h, PSLBM_ERR_PARAM, "staging must be -1, 0 or 1 (1 only where the handle has TMA descriptors)");
+    return fail(h, PSLBM_ERR_PARAM, "staging must be -1, 0, 1 or 2 (1, 2 only where the handle has TMA descriptors)");
   return PSLBM_OK;
 }
 
@@ -1044,7 +1053,7 @@ pslbm_status pslbm_batch_get_tile_shape(pslbm_batch_t b, int32_t* tile_x, int32_
 pslbm_status pslbm_batch_set_staging(pslbm_batch_t b, int32_t mode) {
   if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
   if (set_staging(b->run, mode) != PSLBM_OK)
-    return fail(nullptr, PSLBM_ERR_PARAM, "staging must be -1, 0 or 1 (1 only where every member has TMA descriptors)");
+    return fail(nullptr, PSLBM_ERR_PARAM, "staging must be -1, 0, 1 or 2 (1, 2 only where every member has TMA descriptors)");
   return PSLBM_OK;
 }
 

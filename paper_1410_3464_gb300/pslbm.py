@@ -214,14 +214,15 @@ class Simulation:
         return tx.value, ty.value, bool(tu.value)
 
     def set_staging(self, mode):
-        """-1: choose by timing, 0: plain-load bulk kernel, 1: TMA-staged."""
+        """-1: choose by timing, 0: plain-load bulk kernel, 1: TMA-staged,
+        2: TMA-staged with one stage (three blocks per SM)."""
         _check(load().pslbm_set_staging(self.h, int(mode)), self.h)
 
     def staging(self):
-        """(staged kernel in use, staged kernel available) as booleans."""
+        """(staging in use 0/1/2, staged kernels available)."""
         sg, av = C.c_int32(), C.c_int32()
         _check(load().pslbm_get_staging(self.h, C.byref(sg), C.byref(av)), self.h)
-        return bool(sg.value), bool(av.value)
+        return sg.value, bool(av.value)
 
     def set_step_limit(self, limit):
         _check(load().pslbm_set_step_limit(self.h, int(limit)), self.h)
@@ -313,7 +314,7 @@ class Batch:
     def staging(self):
         sg, av = C.c_int32(), C.c_int32()
         _check(load().pslbm_batch_get_staging(self.b, C.byref(sg), C.byref(av)))
-        return bool(sg.value), bool(av.value)
+        return sg.value, bool(av.value)
 
     def close(self):
         if getattr(self, "b", None):
