@@ -101,14 +101,14 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
         }
         const R w = wf<R>(a);
         // differences from the centre value, in the bulk kernels' operation order
-        const R vp = sv == R(0) ? rmul<R>(w, rsub<R>(ps, psc)) : R(0);
-        const R v2 = sv == R(0) ? rmul<R>(w, rsub<R>(q2, p2c)) : R(0);
-        const R v1 = sv == R(0) ? rmul<R>(w, rsub<R>(q1, p1c)) : R(0);
-        const R vs = rmul<R>(w, sv);
-        stencil_acc<R>(spx, vp, EX(a)); stencil_acc<R>(s2x, v2, EX(a));
-        stencil_acc<R>(s1x, v1, EX(a)); stencil_acc<R>(ssx, vs, EX(a));
-        stencil_acc<R>(spy, vp, EY(a)); stencil_acc<R>(s2y, v2, EY(a));
-        stencil_acc<R>(s1y, v1, EY(a)); stencil_acc<R>(ssy, vs, EY(a));
+        const R dp = sv == R(0) ? rsub<R>(ps, psc) : R(0);
+        const R d2 = sv == R(0) ? rsub<R>(q2, p2c) : R(0);
+        const R d1 = sv == R(0) ? rsub<R>(q1, p1c) : R(0);
+        const R vs = sv == R(0) ? R(0) : w;
+        stencil_acc<R>(spx, w, dp, EX(a)); stencil_acc<R>(s2x, w, d2, EX(a));
+        stencil_acc<R>(s1x, w, d1, EX(a)); stencil_add<R>(ssx, vs, EX(a));
+        stencil_acc<R>(spy, w, dp, EY(a)); stencil_acc<R>(s2y, w, d2, EY(a));
+        stencil_acc<R>(s1y, w, d1, EY(a)); stencil_add<R>(ssy, vs, EY(a));
       }
       const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0], w2 = rp<R>(P).w_adh[1];
       const R F1x = force1<R>(G11, G12, w1, psc, p1c, spx, s2x, ssx, rho1, rp<R>(P).gx);

@@ -184,7 +184,7 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
       uy = jy / rt;
     }
   }
-  const R uu = R(1.5) * (ux * ux + uy * uy);
+  const R uu = half_u2<R>(ux, uy);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const R rho = s == 0 ? r1 : r2;
@@ -195,9 +195,9 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
       if (!is_fluid(s_t[en])) continue;
       // stored relative to the shift of the receiving node's new phase
       const R dr = rho - (s_m[en] ? rp<R>(P).shift_f[s] : rp<R>(P).shift_fg[s]);
-      const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
+      const R eu = R(EX(a)) * ux + R(EY(a)) * uy;   // exact: e has components 0, +-1
       const R w = w9<R>(a);
-      const R feq = w * (dr + rho * (R(3) * eu + R(4.5) * eu * eu - uu));
+      const R feq = feq_shifted<R>(w, dr, rho, eu, uu);
       nbr(P, x, y, EX(a), EY(a), xn, yn);
       st<TF, R>(fo + a * N + yn * P.nx + xn, feq);
     }
@@ -221,8 +221,8 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
         for (int a = 1; a < 5; ++a) {
           const int en = eo + EY(a) * SH::EXT_X + EX(a);
           if (!(is_fluid(s_t[en]) && s_m[en])) continue;
-          const R eu = R(EX(a)) * ux + R(EY(a)) * uy;
-          const R geq = Ja * (Cr[k] - rp<R>(P).shift_c[k]) + R(0.5) * Cr[k] * eu;
+          const R eu = R(EX(a)) * ux + R(EY(a)) * uy;   // exact
+          const R geq = geq_shifted<R>(Ja, Cr[k], rp<R>(P).shift_c[k], eu);
           nbr(P, x, y, EX(a), EY(a), xn, yn);
           st<TG, R>(gout + (k * 5 + a) * N + yn * P.nx + xn, geq);
         }
@@ -287,7 +287,8 @@ struct GlobalSrc {
 // types on entry and the next tile's on return.  Returns true when the block
 // must stop (a bounded wait of the staged kernel gave up in some thread).
 template <class SH, class TF, class TG, class R, int NS, class Src, class AfterSync>
-__device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, const Src& src, AfterSync after_sync,
+__device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, const DevParams& P, const Src& src,
+                                          AfterSync after_sync,
                                           bool waited_ok, TileTypes& tt, const Tile* tiles, int ntiles,
                                           const DevInst* insts, int next_ti, R* sp, R* sq1, R* sq2, uint8_t* st_,
                                           uint8_t* sm_) {
@@ -300,7 +301,6 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     ring_pos<SH>(tid, rex, rey);
     er = rey * SH::EXT_X + rex;
   }
-  const DevParams& P = Ip->P;
   const int N = (int)Ip->N;
   const int nx = P.nx;
   const unsigned long long step = Ip->scal[S_STEP];
@@ -414,14 +414,14 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
       const int en = eo + EY(a) * SH::EXT_X + EX(a);
       const bool lv = is_live(st_[en]);
       const R w = wf<R>(a);
-      const R vp = lv ? rmul<R>(w, rsub<R>(sp[en], psc)) : R(0);
-      const R v2 = lv ? rmul<R>(w, rsub<R>(sq2[en], p2c)) : R(0);
-      const R v1 = lv ? rmul<R>(w, rsub<R>(sq1[en], p1c)) : R(0);
+      const R dp = lv ? rsub<R>(sp[en], psc) : R(0);
+      const R d2 = lv ? rsub<R>(sq2[en], p2c) : R(0);
+      const R d1 = lv ? rsub<R>(sq1[en], p1c) : R(0);
       const R vs = lv ? R(0) : w;
-      stencil_acc<R>(spx, vp, EX(a)); stencil_acc<R>(s2x, v2, EX(a));
-      stencil_acc<R>(s1x, v1, EX(a)); stencil_acc<R>(ssx, vs, EX(a));
-      stencil_acc<R>(spy, vp, EY(a)); stencil_acc<R>(s2y, v2, EY(a));
-      stencil_acc<R>(s1y, v1, EY(a)); stencil_acc<R>(ssy, vs, EY(a));
+      stencil_acc<R>(spx, w, dp, EX(a)); stencil_acc<R>(s2x, w, d2, EX(a));
+      stencil_acc<R>(s1x, w, d1, EX(a)); stencil_add<R>(ssx, vs, EX(a));
+      stencil_acc<R>(spy, w, dp, EY(a)); stencil_acc<R>(s2y, w, d2, EY(a));
+      stencil_acc<R>(s1y, w, d1, EY(a)); stencil_add<R>(ssy, vs, EY(a));
     }
     const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0],
             w2 = rp<R>(P).w_adh[1];
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
     const DevInst* Ip = insts + tl.inst;
     const int cur = int(Ip->scal[S_STEP] & 1ULL);
     const GlobalSrc<TF, TG, R, NS> src{(const TF*)Ip->f[cur], (const TG*)Ip->g[cur], (int)Ip->N};
-    bulk_tile<SH, TF, TG, R, NS>(tl, Ip, src, [] {}, true, tt, tiles, ntiles, insts, nt, s_psi[buf], s_phi1[buf],
+    bulk_tile<SH, TF, TG, R, NS>(tl, Ip, Ip->P, src, [] {}, true, tt, tiles, ntiles, insts, nt, s_psi[buf], s_phi1[buf],
                                  s_phi2[buf], s_t[buf], s_m[buf]);
     buf ^= 1;
     ti = nt;
@@ -724,10 +724,14 @@ __device__ __forceinline__ void stage_issue(const Tile* tiles, const DevInst* in
 // the copy of tile j+1 is issued at tile j's barrier (half the shared memory,
 // three blocks per SM).  The arithmetic is the plain kernel's, value for
 // value.
-template <class SH, int SHAPE, class TG, int NS, int STAGES>
-__global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3) k_bulk_tma(const Tile* __restrict__ tiles,
-                                                                            int ntiles,
-                                                                            const DevInst* __restrict__ insts) {
+//
+// SINGLE: every tile belongs to one simulation, whose parameter block comes
+// as a kernel argument (read from the constant bank, uniform across the
+// grid); otherwise each tile's instance supplies its own block.
+template <class SH, int SHAPE, class TG, int NS, int STAGES, bool SINGLE>
+__global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
+    k_bulk_tma(const Tile* __restrict__ tiles, int ntiles, const DevInst* __restrict__ insts,
+               const __grid_constant__ DevParams Pk) {
   using C = StageCfg<SH, TG, NS>;
   using R = float;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -762,15 +766,16 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3) k_bulk_tma(cons
     const DevInst* Ip = insts + tl.inst;
     const int cur = int(Ip->scal[S_STEP] & 1ULL);
     unsigned char* stage = dyn + b * C::STAGE;
+    const DevParams& P = SINGLE ? Pk : Ip->P;
     const StageSrc<SH, TG, NS> src{(const float*)(stage + C::FOFF), (const TG*)(stage + C::GOFF),
-                                   (const float*)Ip->f[cur], (int)Ip->N, Ip->P.nx, Ip->P.ny, tl.x0, tl.y0};
+                                   (const float*)Ip->f[cur], (int)Ip->N, P.nx, P.ny, tl.x0, tl.y0};
     // after the tile's barrier its stage is free: refill it with the next
     // tile this stage serves
     const int tn = STAGES == 2 ? t2 : t1;
     auto refill = [&] {
       if (threadIdx.x == 0 && tn < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, tn, stage, &bars[b]);
     };
-    if (bulk_tile<SH, float, TG, R, NS>(tl, Ip, src, refill, ok, tt, tiles, ntiles, insts, t1, s_psi[sb], s_phi1[sb],
+    if (bulk_tile<SH, float, TG, R, NS>(tl, Ip, P, src, refill, ok, tt, tiles, ntiles, insts, t1, s_psi[sb], s_phi1[sb],
                                         s_phi2[sb], s_t[sb], s_m[sb])) {
       // a wait gave up: record it, let the copies still in flight land
       // (bounded waits: this tile's stage, and with two stages the next

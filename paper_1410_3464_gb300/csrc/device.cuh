@@ -283,13 +283,37 @@ __device__ __forceinline__ bool outlet_up_liquid(const DevParams& P, const uint8
   return liquid_at<R, TF>(P, tin, fin, N, yn * P.nx + xn, theta);
 }
 
+// Explicitly rounded operations.  The hot formulas are written with these
+// (fused where a product feeds a sum) so that the compiler cannot contract
+// them differently in different kernel variants: every variant -- plain
+// loads, TMA stages, parameters from global memory or from the constant bank
+// -- evaluates exactly the same operations and gives bit-identical results.
+template <class R> __device__ __forceinline__ R radd(R a, R b);
+template <class R> __device__ __forceinline__ R rsub(R a, R b);
+template <class R> __device__ __forceinline__ R rmul(R a, R b);
+template <class R> __device__ __forceinline__ R rdiv(R a, R b);
+template <class R> __device__ __forceinline__ R rfma(R a, R b, R c);
+template <> __device__ __forceinline__ float radd<float>(float a, float b) { return __fadd_rn(a, b); }
+template <> __device__ __forceinline__ float rsub<float>(float a, float b) { return __fsub_rn(a, b); }
+template <> __device__ __forceinline__ float rmul<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ float rdiv<float>(float a, float b) { return __fdiv_rn(a, b); }
+template <> __device__ __forceinline__ float rfma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double radd<double>(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ double rsub<double>(double a, double b) { return __dsub_rn(a, b); }
+template <> __device__ __forceinline__ double rmul<double>(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ double rdiv<double>(double a, double b) { return __ddiv_rn(a, b); }
+template <> __device__ __forceinline__ double rfma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Eq. 12 (C-S EOS) and the Eq. 13 square-root argument 6/G11 (p - rho/3).
 template <class R> __device__ __forceinline__ R psi_arg(const DevParams& P, R rho) {
+  // Eq. 12 with 1 + eta + eta^2 - eta^3 = 1 + eta (1 + eta (1 - eta))
   const DevParamsR<R>& Q = rp<R>(P);
-  const R eta = Q.eos_b4 * rho;
-  const R om = R(1) - eta;
-  const R p = rho * Q.eos_RT * (R(1) + eta + eta * eta - eta * eta * eta) / (om * om * om) - Q.eos_a * rho * rho;
-  return Q.six_over_G11 * (p - rho / R(3));
+  const R eta = rmul<R>(Q.eos_b4, rho);
+  const R om = rsub<R>(R(1), eta);
+  const R poly = rfma<R>(eta, rfma<R>(eta, om, R(1)), R(1));
+  const R num = rmul<R>(rmul<R>(rho, Q.eos_RT), poly);
+  const R p = rfma<R>(-rmul<R>(Q.eos_a, rho), rho, rdiv<R>(num, rmul<R>(rmul<R>(om, om), om)));
+  return rmul<R>(Q.six_over_G11, rsub<R>(p, rdiv<R>(rho, R(3))));
 }
 
 template <class R> __device__ __forceinline__ R rrcp(R v);
@@ -301,36 +325,35 @@ template <> __device__ __forceinline__ float rmax<float>(float a, float b) { ret
 template <class R> __device__ __forceinline__ R rexp(R v);
 template <> __device__ __forceinline__ double rexp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float rexp<float>(float v) { return expf(v); }
-// Arithmetic helpers of the force, velocity and collision formulas (plain
-// operators: the compiler may fuse a product into a following sum; every bulk
-// kernel variant runs the same tile body, so all variants round identically).
-template <class R> __device__ __forceinline__ R radd(R a, R b) { return a + b; }
-template <class R> __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
-template <class R> __device__ __forceinline__ R rmul(R a, R b) { return a * b; }
-template <class R> __device__ __forceinline__ R rfma(R a, R b, R c) { return a * b + c; }
 
-// One term of the force stencils: accumulate +-w (v_n - v_c) along one axis
-// (dir = +1, -1 or 0; a constant once the direction loop is unrolled).
+// One term of the force stencils along one axis (dir = +1, -1 or 0, a
+// constant once the direction loop is unrolled): s += dir w d (fused), and the
+// wall-density stencil s += dir v.
 template <class R>
-__device__ __forceinline__ void stencil_acc(R& s, R wv, int dir) {
-  if (dir > 0) s = radd<R>(s, wv);
-  if (dir < 0) s = rsub<R>(s, wv);
+__device__ __forceinline__ void stencil_acc(R& s, R w, R d, int dir) {
+  if (dir > 0) s = rfma<R>(w, d, s);
+  if (dir < 0) s = rfma<R>(-w, d, s);
+}
+template <class R>
+__device__ __forceinline__ void stencil_add(R& s, R v, int dir) {
+  if (dir > 0) s = radd<R>(s, v);
+  if (dir < 0) s = rsub<R>(s, v);
 }
 
 // F_1 (Eqs. 11, 14a, 16 and the body force) from its stencil sums, and F_2
 // (Eqs. 14b, 16), in a fixed operation order.
 template <class R>
 __device__ __forceinline__ R force1(R G11, R G12, R w1, R psc, R p1c, R sp, R s2, R ss, R rho1, R g) {
-  const R a = rmul<R>(rmul<R>(G11, psc), sp);
-  const R b = rmul<R>(rmul<R>(G12, p1c), s2);
-  const R c = rmul<R>(rmul<R>(w1, psc), ss);
-  return radd<R>(rsub<R>(rsub<R>(-a, b), c), rmul<R>(rho1, g));
+  R F = -rmul<R>(rmul<R>(G11, psc), sp);
+  F = rfma<R>(-rmul<R>(G12, p1c), s2, F);
+  F = rfma<R>(-rmul<R>(w1, psc), ss, F);
+  return rfma<R>(rho1, g, F);
 }
 template <class R>
 __device__ __forceinline__ R force2(R G21, R w2, R p2c, R s1, R ss, R rho2, R g) {
-  const R a = rmul<R>(rmul<R>(G21, p2c), s1);
-  const R c = rmul<R>(rmul<R>(w2, rho2), ss);
-  return radd<R>(rsub<R>(-a, c), rmul<R>(rho2, g));
+  R F = -rmul<R>(rmul<R>(G21, p2c), s1);
+  F = rfma<R>(-rmul<R>(w2, rho2), ss, F);
+  return rfma<R>(rho2, g, F);
 }
 
 // Common velocity u' (Eq. 18) of one axis, and u_r (Eq. 19).
@@ -391,8 +414,8 @@ __device__ __forceinline__ void potentials(const DevParams& P, R rho1, R rho2, R
   } else {
     psi = R(0);
   }
-  phi1 = -rexpm1<R>(-rho2 * Q.inv_rho20);
-  phi2 = Q.a0 - rexp<R>(-rho1 * Q.inv_rho10);
+  phi1 = -rexpm1<R>(-rmul<R>(rho2, Q.inv_rho20));
+  phi2 = rsub<R>(Q.a0, rexp<R>(-rmul<R>(rho1, Q.inv_rho10)));
 }
 
 // Same as potentials(), with the parameters taken from a block already staged
@@ -413,8 +436,8 @@ __device__ __forceinline__ void potentials_q(const DevParamsR<R>& Q, bool has_G1
   } else {
     psi = R(0);
   }
-  phi1 = -rexpm1<R>(-rho2 * Q.inv_rho20);
-  phi2 = Q.a0 - rexp<R>(-rho1 * Q.inv_rho10);
+  phi1 = -rexpm1<R>(-rmul<R>(rho2, Q.inv_rho20));
+  phi2 = rsub<R>(Q.a0, rexp<R>(-rmul<R>(rho1, Q.inv_rho10)));
 }
 
 // SplitMix64 output for a given state (Steele, Lea, Flood 2014).

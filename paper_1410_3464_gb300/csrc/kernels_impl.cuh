@@ -31,21 +31,39 @@ void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts)
 // Staged variants: grid of as many blocks as fit (two per SM with the
 // double-buffered stage, three with the single stage), dynamic shared memory
 // opted in once.
-template <class SH, int SHAPE, int NS, int STAGES>
-void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
-  if (ntiles <= 0) return;
+template <class SH, int SHAPE, int NS, int STAGES, bool SINGLE>
+int bulk_tma_cap() {
   using C = StageCfg<SH, KTG, NS>;
   constexpr int smem = STAGES * C::STAGE;
   static int cap = 0;
   if (cap == 0) {
-    cudaFuncSetAttribute(k_bulk_tma<SH, SHAPE, KTG, NS, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto k = k_bulk_tma<SH, SHAPE, KTG, NS, STAGES, SINGLE>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk_tma<SH, SHAPE, KTG, NS, STAGES>, NTHREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NTHREADS, smem);
     cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
-  k_bulk_tma<SH, SHAPE, KTG, NS, STAGES><<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts);
+  return cap;
+}
+// single: the parameter block of the only simulation of the tile list (host
+// copy, passed by value), or null for a batch.
+template <class SH, int SHAPE, int NS, int STAGES>
+void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts, const DevParams* single) {
+  if (ntiles <= 0) return;
+  using C = StageCfg<SH, KTG, NS>;
+  constexpr int smem = STAGES * C::STAGE;
+  if (single) {
+    const int cap = bulk_tma_cap<SH, SHAPE, NS, STAGES, true>();
+    k_bulk_tma<SH, SHAPE, KTG, NS, STAGES, true>
+        <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, *single);
+  } else {
+    static const DevParams unused{};
+    const int cap = bulk_tma_cap<SH, SHAPE, NS, STAGES, false>();
+    k_bulk_tma<SH, SHAPE, KTG, NS, STAGES, false>
+        <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, unused);
+  }
 }
 template <class SH, int NS>
 void vop_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {

@@ -7,10 +7,11 @@ namespace pslbm {
 
 struct Launchers {
   void (*bulk[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
-  // TMA-staged bulk kernel (FP32 populations only; null for FP64)
-  void (*bulk_tma[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
+  // TMA-staged bulk kernel (FP32 populations only; null for FP64); single is
+  // the host parameter block when the tile list holds one simulation, else null
+  void (*bulk_tma[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*, const DevParams* single);
   // TMA-staged bulk kernel with a single stage and three blocks per SM
-  void (*bulk_tma1[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
+  void (*bulk_tma1[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*, const DevParams* single);
   void (*vop[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
   void (*amend)(cudaStream_t, int ninst, const DevInst*);
   void (*init)(cudaStream_t, DevInst*, const uint8_t*, const double*, const double*, const double*, long long N);

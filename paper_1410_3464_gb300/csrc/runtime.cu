@@ -59,6 +59,7 @@ struct Stepper {
   int fix_shape = -1;                      // caller's choice, -1: choose by timing
   int fix_staged = -1;
   bool staged_ok = false;                  // every instance has TMA descriptors
+  const DevParams* single = nullptr;       // host parameters of a one-simulation stepper
   bool tuned = false;                      // variant chosen (by timing or by the caller)
   GraphCache graphs;
   double trial_ms[NSHAPES][NSTAGING] = {};
@@ -344,9 +345,13 @@ void free_all(pslbm_t h) {
 
 // Enqueue n steps of the kernels for one bulk-kernel variant.
 void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int staged, int64_t n) {
-  auto bulk = staged == 2 ? st.L->bulk_tma1[shape] : staged == 1 ? st.L->bulk_tma[shape] : st.L->bulk[shape];
   for (int64_t i = 0; i < n; ++i) {
-    bulk(s, st.tiles[shape], st.ntiles[shape], st.d);
+    if (staged == 2)
+      st.L->bulk_tma1[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
+    else if (staged == 1)
+      st.L->bulk_tma[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
+    else
+      st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
     st.L->vop[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
     st.L->amend(s, st.ninst, st.d);
   }
@@ -730,6 +735,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   h->run.d = h->d;
   h->run.ninst = 1;
   h->run.dims.assign(1, {p->nx, p->ny});
+  h->run.single = &h->h.P;
   choose(h->run);
   {
     cudaError_t e = ensure_tiles(h->run, h->run.shape);
@@ -782,9 +788,12 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
   for (int64_t i = 0; i < n && st == PSLBM_OK; ++i) {
     const int sh = h->run.shape;
     cudaEventRecord(ev[0], s);
-    (h->run.staged == 2   ? h->L->bulk_tma1[sh]
-     : h->run.staged == 1 ? h->L->bulk_tma[sh]
-                          : h->L->bulk[sh])(s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
+    if (h->run.staged == 2)
+      h->L->bulk_tma1[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, &h->h.P);
+    else if (h->run.staged == 1)
+      h->L->bulk_tma[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, &h->h.P);
+    else
+      h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[1], s);
     h->L->vop[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[2], s);
