@@ -237,13 +237,16 @@ def ours_arm(args):
         peaks = json.load(open(pk_path))
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = bytes_per_launch / (bulk_ms * 1e-3) / 1e9
-    traffic = None
-    if os.path.exists(PROFILE_JSON) and prec == pslbm.FP32:
-        pj = json.load(open(PROFILE_JSON))
-        if pj.get("source_hash") == kernel_source_hash():
-            traffic = pj.get("dram_bytes_per_launch")
     tshape = sim.tile_shape()
     staged = sim.staging()[0]
+    variant = f"{tshape[0]}x{tshape[1]} {STAGING_NAMES[staged]}"
+    traffic = None
+    if os.path.exists(PROFILE_JSON) and prec == pslbm.FP32:
+        # DRAM bytes per launch from an ncu capture of the same kernel variant
+        # built from the same sources (null otherwise)
+        pj = json.load(open(PROFILE_JSON))
+        if pj.get("source_hash") == kernel_source_hash():
+            traffic = pj.get("traffic_per_launch", {}).get(variant)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": KERNEL_NAMES[staged], "bytes_per_launch": bytes_per_launch,
                 "kernel_ms": bulk_ms, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",

@@ -117,21 +117,11 @@ def _splitmix64_stream(seed):
 
 def _liquid_spans_x(open_):
     """True if a 4-connected path of open nodes joins column 0 to the last column."""
-    ny, nx = open_.shape
-    seen = np.zeros_like(open_)
-    stack = [(yy, 0) for yy in range(ny) if open_[yy, 0]]
-    for s in stack:
-        seen[s] = True
-    while stack:
-        yy, xx = stack.pop()
-        if xx == nx - 1:
-            return True
-        for dy, dx in ((0, 1), (1, 0), (0, -1), (-1, 0)):
-            a, b = yy + dy, xx + dx
-            if 0 <= a < ny and 0 <= b < nx and open_[a, b] and not seen[a, b]:
-                seen[a, b] = True
-                stack.append((a, b))
-    return False
+    from scipy import ndimage
+    lab, _ = ndimage.label(open_, structure=[[0, 1, 0], [1, 1, 1], [0, 1, 0]])
+    left = set(np.unique(lab[:, 0])) - {0}
+    right = set(np.unique(lab[:, -1])) - {0}
+    return bool(left & right)
 
 
 def discs_mask(nx, ny, seed, rmin=8.0, rmax=24.0, porosity=0.6, buffer=16, walls=True):
@@ -148,13 +138,15 @@ def discs_mask(nx, ny, seed, rmin=8.0, rmax=24.0, porosity=0.6, buffer=16, walls
         target = 1.0 - porosity
         interior = (x >= lo) & (x < hi)
         area = interior.sum()
-        while solid[interior].sum() < target * area:
+        count = 0                      # solid nodes of the interior, kept incrementally
+        while count < target * area:
             cx = lo + next(rng) * (hi - lo)
             cy = next(rng) * ny
             r = rmin + next(rng) * (rmax - rmin)
             x0, x1 = max(int(cx - r) - 1, lo), min(int(cx + r) + 2, hi)
             y0, y1 = max(int(cy - r) - 1, 0), min(int(cy + r) + 2, ny)
             sub = (x[y0:y1, x0:x1] - cx) ** 2 + (y[y0:y1, x0:x1] - cy) ** 2 <= r * r
+            count += int((sub & ~solid[y0:y1, x0:x1]).sum())
             solid[y0:y1, x0:x1] |= sub
         mask = np.where(solid, SOLID_D, LIQUID).astype(np.uint8)
         if walls:
@@ -199,8 +191,12 @@ def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
             if pore[int(cy), int(cx)]:
                 break
         r = bubble_r[0] + next(rng) * (bubble_r[1] - bubble_r[0])
-        d = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
-        prof = np.maximum(prof, 0.5 * (1.0 - np.tanh((d - r) / 2.0)))
+        # the tanh profile is below 3e-9 beyond r + 20: evaluate it in a window
+        h = int(r) + 21
+        x0, x1 = max(int(cx) - h, 0), min(int(cx) + h + 1, nx)
+        y0, y1 = max(int(cy) - h, 0), min(int(cy) + h + 1, ny)
+        d = np.sqrt((x[y0:y1, x0:x1] - cx) ** 2 + (y[y0:y1, x0:x1] - cy) ** 2)
+        prof[y0:y1, x0:x1] = np.maximum(prof[y0:y1, x0:x1], 0.5 * (1.0 - np.tanh((d - r) / 2.0)))
     prof = np.where(pore, prof, 0.0)
     mask[pore & (prof > 0.5)] = GAS
     fluid = (mask == LIQUID) | (mask == GAS)

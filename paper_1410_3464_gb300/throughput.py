@@ -1,0 +1,141 @@
+"""Throughput of the FP32 path on the large-lattice and batched workloads.
+
+    python -m paper_1410_3464_gb300.throughput --workload large --steps 300
+        porous discs 4096x2048 (seed 3), one simulation
+    python -m paper_1410_3464_gb300.throughput --workload batch --instances 256 --steps 300
+        independent porous geometries (seed 4), sides log-uniform 128-1024
+        (multiples of 16), porosity U[0.4, 0.8], rates log-uniform 1e-6-1e-1,
+        stepped together as one batch (one launch per kernel per step over the
+        packed tile list, CUDA graphs of up to 32 steps)
+
+Both working sets exceed the 129 MB L2 by an order of magnitude, so no flush
+is needed between steps.  The step count is timed with CUDA events on the
+library stream after the variant autotuning and a warm-up; the JSON line
+gives MLUPS over all nodes, the algorithmic bytes of the bulk kernel (fluid
+nodes x 144 B + liquid nodes x 120 B + 2 B per node for FP32 with three
+species) per step, the achieved GB/s of the whole step against the measured
+HBM bandwidth, and the chosen kernel variant.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import inputs, pslbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma 1-stage"}
+
+
+def peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def step_bytes(types, ns, fs=4, gs=4):
+    n_fluid = int((types <= 1).sum())
+    n_liq = int((types == 0).sum())
+    return n_fluid * 36 * fs + n_liq * 10 * ns * gs + 2 * types.size, n_fluid, n_liq
+
+
+def timed(run_steps, steps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        run_steps(steps)
+        b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) * 1e-3
+
+
+def large(args):
+    import torch
+    stream = torch.cuda.ExternalStream(pslbm.get_stream())
+    t0 = time.time()
+    sc = inputs.porous_discs(nx=args.nx, ny=args.ny, seed=args.seed)
+    gen_s = time.time() - t0
+    with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                          precision=pslbm.FP32) as s:
+        s.step(40)                       # autotuning (24 steps) and warm-up
+        s.sync()
+        el = timed(s.step, args.steps, stream)
+        s.sync()
+        types = s.read(pslbm.F_TYPE)["type"]
+        tx, ty, _ = s.tile_shape()
+        staged = s.staging()[0]
+    nbytes, nf, nl = step_bytes(types, sc["params"]["n_species"])
+    N = args.nx * args.ny
+    pk, src = peak_gbs()
+    gbs = nbytes * args.steps / el / 1e9
+    return dict(workload=f"porous discs {args.nx}x{args.ny} (seed {args.seed}), FP32, one simulation",
+                nodes=N, fluid_nodes=nf, liquid_nodes=nl, steps=args.steps, seconds=el,
+                mlups=N * args.steps / el / 1e6, ms_per_step=1e3 * el / args.steps,
+                bulk_bytes_per_step=nbytes, step_gbs=gbs, peak_gbs=pk, peak_source=src, frac_of_peak=gbs / pk,
+                tile=f"{tx}x{ty}", staging=STAGING_NAMES[staged], scene_generation_s=gen_s)
+
+
+def batch(args):
+    import torch
+    stream = torch.cuda.ExternalStream(pslbm.get_stream())
+    reqs = inputs.request_stream(args.instances, seed=args.seed, size_range=(128, 1024),
+                                 budget_range=(1000, 10000), rate_range=(1e-6, 1e-1),
+                                 porosity_range=(0.4, 0.8), stop_fraction=0.0)
+    t0 = time.time()
+    scenes = [inputs.request_scene(r) for r in reqs]
+    gen_s = time.time() - t0
+    sims = [pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                             precision=pslbm.FP32) for sc in scenes]
+    b = pslbm.Batch(sims)
+    b.step(40)                           # autotuning and warm-up
+    b.sync()
+    el = timed(b.step, args.steps, stream)
+    b.sync()
+    tx, ty, _ = b.tile_shape()
+    staged = b.staging()[0]
+    b.close()
+    nbytes = nf = nl = N = 0
+    for s, sc in zip(sims, scenes):
+        t = s.read(pslbm.F_TYPE)["type"]
+        bb, f, l = step_bytes(t, sc["params"]["n_species"])
+        nbytes += bb
+        nf += f
+        nl += l
+        N += t.size
+        s.close()
+    pk, src = peak_gbs()
+    gbs = nbytes * args.steps / el / 1e9
+    sides = np.array([(r["nx"], r["ny"]) for r in reqs])
+    return dict(workload=(f"{args.instances} porous geometries (seed {args.seed}), sides log-uniform 128-1024, "
+                          f"porosity U[0.4,0.8], rates log-uniform 1e-6-1e-1, FP32, one batch"),
+                instances=args.instances, nodes=N, fluid_nodes=nf, liquid_nodes=nl,
+                mean_nodes_per_instance=N / args.instances, min_side=int(sides.min()), max_side=int(sides.max()),
+                steps=args.steps, seconds=el, mlups=N * args.steps / el / 1e6, ms_per_step=1e3 * el / args.steps,
+                bulk_bytes_per_step=nbytes, step_gbs=gbs, peak_gbs=pk, peak_source=src, frac_of_peak=gbs / pk,
+                tile=f"{tx}x{ty}", staging=STAGING_NAMES[staged], scene_generation_s=gen_s)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", choices=["large", "batch"], default="large")
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--steps", type=int, default=300)
+    args = ap.parse_args(argv)
+    if args.seed is None:
+        args.seed = 3 if args.workload == "large" else 4
+    out = large(args) if args.workload == "large" else batch(args)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
