@@ -203,6 +203,16 @@ pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, i
 pslbm_status pslbm_set_staging(pslbm_t h, int32_t mode);
 pslbm_status pslbm_get_staging(pslbm_t h, int32_t* staged, int32_t* available);
 
+/* Per-step monitor: the number of steps taken, the maximum liquid-component
+ * density over fluid nodes found by the last step (the quantity whose half is
+ * the next liquid threshold, Section 4.5; the initial maximum before the first
+ * step) and the device status bits (1 non-finite density, 2 EOS domain,
+ * 4 event-list overflow, 8 staged-copy timeout).  Reads 64 bytes from the
+ * device and synchronises the library stream; no kernel runs.  Returns the
+ * matching error status when a bit is set (sticky, as for pslbm_sync).  Any
+ * output pointer may be NULL. */
+pslbm_status pslbm_monitor(pslbm_t h, int64_t* steps, double* max_rho1, uint32_t* status);
+
 /* Number of steps taken and lattice size. */
 pslbm_status pslbm_info(pslbm_t h, int64_t* steps, int32_t* nx, int32_t* ny, int32_t* n_species);
 

@@ -871,6 +871,24 @@ pslbm_status pslbm_get_staging(pslbm_t h, int32_t* staged, int32_t* available) {
   return PSLBM_OK;
 }
 
+pslbm_status pslbm_monitor(pslbm_t h, int64_t* steps, double* max_rho1, uint32_t* status) {
+  if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  if (h->sticky) return h->sticky;
+  unsigned long long sc[S_NSCAL];
+  CK(h, cudaMemcpyAsync(sc, h->h.scal, sizeof sc, cudaMemcpyDeviceToHost, lib_stream()));
+  CK(h, cudaStreamSynchronize(lib_stream()));
+  const unsigned long long n = sc[S_STEP];
+  if (steps) *steps = (int64_t)n;
+  // the slot the last step filled (the initial maximum before the first step)
+  if (max_rho1) *max_rho1 = ord_dec(sc[S_MAX0 + int(n & 1ULL)]);
+  if (status) *status = (uint32_t)sc[S_STATUS];
+  if (sc[S_STATUS] & ST_NONFINITE) return fail(h, PSLBM_ERR_NONFINITE, "non-finite density on the device");
+  if (sc[S_STATUS] & ST_EOS)
+    return fail(h, PSLBM_ERR_EOS_DOMAIN, "Eq. 13 square-root argument negative (rho_1 outside the EOS domain)");
+  if (sc[S_STATUS] & ST_TIMEOUT) return fail(h, PSLBM_ERR_TIMEOUT, "a bounded wait for staged populations gave up");
+  return PSLBM_OK;
+}
+
 pslbm_status pslbm_sync(pslbm_t h) {
   if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
   if (h->sticky) return h->sticky;

@@ -159,7 +159,7 @@ def discs_mask(nx, ny, seed, rmin=8.0, rmax=24.0, porosity=0.6, buffer=16, walls
 
 def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
                  k1=1e-5, k3=1e-1, k2=1e-3, k4=1e-3, rho2_gas=0.002, rho2_liq=2e-5,
-                 bubbles=None, bubble_r=(4.0, 10.0), slug=None, overpressure=1.01):
+                 bubbles=None, bubble_r=(4.0, 10.0), slug=None, overpressure=1.01, gas_mass=0.1):
     """Porous-medium scene: pressure-driven flow in x through seeded overlapping
     D(s) discs, with gas slugs in the pore space carried by the flow.
 
@@ -176,7 +176,7 @@ def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
     rl, rg = COEX_ORIGINAL_07
     # mass units of Eq. 25b: C_A = 1 in liquid at rho_l, so M_A = rho_l; the gas
     # C(g) of R1 is light, M_C = 0.1 M_A (Eq. 27: S_2 = -S_1 = 0.5 R1 M_C)
-    m_gas = 0.1 * rl
+    m_gas = gas_mass * rl
     y, x = np.mgrid[0:ny, 0:nx]
     pore = mask == LIQUID
     rng = _splitmix64_stream(seed * 7919 + 17)

@@ -30,7 +30,8 @@ EXPORTS = ["pslbm_get_stream", "pslbm_set_stream", "pslbm_create", "pslbm_step",
            "pslbm_server_create", "pslbm_server_submit", "pslbm_server_advance", "pslbm_server_poll",
            "pslbm_server_fetch", "pslbm_server_release", "pslbm_server_last_error", "pslbm_server_destroy",
            "pslbm_set_tile_shape", "pslbm_get_tile_shape", "pslbm_batch_get_tile_shape",
-           "pslbm_set_staging", "pslbm_get_staging", "pslbm_batch_set_staging", "pslbm_batch_get_staging"]
+           "pslbm_set_staging", "pslbm_get_staging", "pslbm_batch_set_staging", "pslbm_batch_get_staging",
+           "pslbm_monitor"]
 
 _D2 = C.c_double * 2
 _DS = C.c_double * MAX_SPECIES
@@ -139,6 +140,7 @@ def load():
     lib.pslbm_get_tile_shape.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.pslbm_batch_get_tile_shape.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.pslbm_set_staging.argtypes = [vp, i32]
+    lib.pslbm_monitor.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_uint32)]
     lib.pslbm_get_staging.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     lib.pslbm_batch_set_staging.argtypes = [vp, i32]
     lib.pslbm_batch_get_staging.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
@@ -223,6 +225,13 @@ class Simulation:
         sg, av = C.c_int32(), C.c_int32()
         _check(load().pslbm_get_staging(self.h, C.byref(sg), C.byref(av)), self.h)
         return sg.value, bool(av.value)
+
+    def monitor(self):
+        """(steps taken, maximum rho_1 found by the last step, status bits):
+        a 64-byte read, no kernel."""
+        n, m, st = C.c_int64(), C.c_double(), C.c_uint32()
+        _check(load().pslbm_monitor(self.h, C.byref(n), C.byref(m), C.byref(st)), self.h)
+        return n.value, m.value, st.value
 
     def set_step_limit(self, limit):
         _check(load().pslbm_set_step_limit(self.h, int(limit)), self.h)

@@ -1,7 +1,7 @@
 """Throughput of the FP32 path on the large-lattice and batched workloads.
 
     python -m paper_1410_3464_gb300.throughput --workload large --steps 300
-        porous discs 4096x2048 (seed 3), one simulation
+        porous discs 4096x2048 (seed 1), one simulation
     python -m paper_1410_3464_gb300.throughput --workload batch --instances 256 --steps 300
         independent porous geometries (seed 4), sides log-uniform 128-1024
         (multiples of 16), porosity U[0.4, 0.8], rates log-uniform 1e-6-1e-1,
@@ -132,7 +132,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=300)
     args = ap.parse_args(argv)
     if args.seed is None:
-        args.seed = 3 if args.workload == "large" else 4
+        args.seed = 1 if args.workload == "large" else 4
     out = large(args) if args.workload == "large" else batch(args)
     print(json.dumps(out), flush=True)
 
