@@ -106,14 +106,26 @@ def study(args):
         precs = precs + ["fp64_perturbed"]
     rows = []
     done = 0
+    failed = {}
     t0 = time.time()
     for c in checkpoints:
-        for s in sims.values():
-            s.step(c - done)
+        for name, s in list(sims.items()):
+            try:
+                s.step(c - done)
+                s.sync()
+            except pslbm.PslbmError as e:      # a run that diverged is reported and dropped
+                failed[name] = f"between steps {done} and {c}: {e}"
+                s.close()
+                del sims[name]
         done = c
+        row = {"step": c, "failed": dict(failed)}
+        if "fp64" not in sims:
+            rows.append(row)
+            break
         ref = sims["fp64"].read()
-        row = {"step": c}
         for p in precs:
+            if p not in sims:
+                continue
             got = sims[p].read()
             row[p] = field_errors(got, ref)
             row[p]["budget_rel"] = [float(abs(g - r) / max(abs(r), 1e-300))
@@ -121,13 +133,13 @@ def study(args):
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
         if args.save_fields:
-            np.savez_compressed(f"{args.save_fields}_{c}.npz", **{f"{p}_{k}": v for p in ["fp64"] + precs
+            np.savez_compressed(f"{args.save_fields}_{c}.npz", **{f"{p}_{k}": v for p in ["fp64"] + precs if p in sims
                                 for k, v in sims[p].read().items()})
     for s in sims.values():
         s.close()
     return {"scene": args.scene, "nx": args.nx, "ny": args.ny, "seed": args.seed,
             "rho_ref": list(sc["params"]["rho_ref"]), "conc_ref": list(sc["params"]["conc_ref"]),
-            "perturb": args.perturb, "wall_s": time.time() - t0, "rows": rows}
+            "perturb": args.perturb, "failed": failed, "wall_s": time.time() - t0, "rows": rows}
 
 
 def main(argv=None):
