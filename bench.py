@@ -56,12 +56,13 @@ def parse():
 
 
 def kernel_source_hash():
+    """Hash of the device-code sources the bulk kernels are compiled from (an
+    ncu traffic figure is only reported for a build of these same files)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1410_3464_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ("device.cuh", "tma.cuh", "bulk.cuh", "kernels_impl.cuh", "kernels_f32.cu"):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
