@@ -538,6 +538,9 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
           st<TF, R>(fo + a * N + nb[a], rfma<R>(w, sm_[en] ? dl : dg, fs));
         else if (!is_res(tn))
           st<TF, R>(fo + OPP(a) * N + node, rfma<R>(w, down, fs));
+        // a liquid node flags the minerals on its axis links for the VOP kernel
+        if (s == 0 && a < 5 && liq && is_mineral(tn))
+          atomicOr(&Ip->vmask[nb[a] >> 5], 1u << (nb[a] & 31));
       }
     }
 

@@ -115,6 +115,8 @@ struct DevInst {
   double* xs;                 // [N] overflow excess of an event node
   int* evlist;                // [evcap] event node indices
   int* claim;                 // [N] zero except while the amendment kernel runs
+  unsigned* vmask;            // [(N + 31) / 32] bit per node: a mineral a liquid node touched this
+                              // step (set by the bulk kernel, consumed and cleared by k_vop)
   unsigned long long* scal;   // [S_NSCAL]
   long long N;
   int evcap;

@@ -20,107 +20,134 @@ namespace pslbm {
 // D(s) or F(s)); E gains the B consumed on the same link.  Then V_D -= Vbar_D
 // sum q_B, V_F += Vbar_F sum q_F, and the node dissolves, overflows or changes
 // between D(s) and F(s).
-template <class SH, class TF, class TG, class R, int NS>
-__global__ void __launch_bounds__(NTHREADS) k_vop(const Tile* __restrict__ tiles, int ntiles,
-                                                   const DevInst* __restrict__ insts) {
-  const int tid = threadIdx.x;
-  const int tx = tid % SH::TX, ty = tid / SH::TX;
-  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    const Tile tl = tiles[ti];
-    const DevInst* Ip = insts + tl.inst;
-    const DevParams& P = Ip->P;
-    const int x = tl.x0 + tx, y = tl.y0 + ty;
-    if (x >= P.nx || y >= P.ny) continue;
-    const int N = (int)Ip->N;
-    const unsigned long long step = Ip->scal[S_STEP];
-    if (step >= Ip->scal[S_LIMIT]) continue;   // frozen instance
-    const int cur = int(step & 1ULL);
-    uint8_t* tnew = Ip->type[cur ^ 1];
-    const int node = y * P.nx + x;
-    const uint8_t t = tnew[node] & T_MASK;
-    if (!is_mineral(t)) continue;
-    int nbx[4];
-    int nl = 0;
-    int dirs[4];
+//
+// The bulk kernel sets a bit for every mineral node a liquid node touched in
+// the step (the only nodes this kernel changes); each warp takes one 32-bit
+// word of that bitmap, lane i handles node 32 w + i when its bit is set, and
+// lane 0 clears the word.
+template <class TF, class TG, class R, int NS>
+__device__ __forceinline__ void vop_node(const DevInst* Ip, const DevParams& P, int N, int cur,
+                                         unsigned long long step, int node) {
+  uint8_t* __restrict__ tnew = Ip->type[cur ^ 1];
+  double* __restrict__ V = Ip->V;
+  // independent loads first: own type, volumes, the four neighbour types
+  const uint8_t t = tnew[node] & T_MASK;
+  double VD = V[node], VF = V[N + node];
+  const int x = node % P.nx, y = node / P.nx;
+  int nbx[4];
+#pragma unroll
+  for (int b = 1; b < 5; ++b) {
+    int xn, yn;
+    nbx[b - 1] = nbr(P, x, y, EX(b), EY(b), xn, yn) ? yn * P.nx + xn : -1;
+  }
+  uint8_t tn[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) tn[b] = nbx[b] >= 0 ? (tnew[nbx[b]] & T_MASK) : T_WALL;
+  if (!is_mineral(t)) return;
+  int nl = 0;
+  int dirs[4];
+#pragma unroll
+  for (int b = 1; b < 5; ++b) {
+    if (tn[b - 1] != T_LIQUID) nbx[b - 1] = -1;
+    else dirs[nl++] = b;
+  }
+  if (nl == 0) return;
+  R sB = R(0), sF = R(0);
+  if constexpr (NS > 0) {
+    TG* __restrict__ gout = (TG*)Ip->g[cur ^ 1];
+    const bool useB = (t == T_SOLID_D) && P.useB;
+    const bool useF = P.useF != 0;
+    // the population that left neighbour nn toward this node was bounced into
+    // slot b of nn; gather every slot before writing any
+    R oB[4], oE[4], oF[4];
 #pragma unroll
     for (int b = 1; b < 5; ++b) {
-      int xn, yn;
-      nbx[b - 1] = -1;
-      if (!nbr(P, x, y, EX(b), EY(b), xn, yn)) continue;
-      const int nn = yn * P.nx + xn;
-      if ((tnew[nn] & T_MASK) != T_LIQUID) continue;
-      nbx[b - 1] = nn;
-      dirs[nl++] = b;
+      const int nn = nbx[b - 1];
+      oB[b - 1] = oE[b - 1] = oF[b - 1] = R(0);
+      if (nn < 0) continue;
+      if (useB) {
+        oB[b - 1] = ldc<R>(gout + (P.iB * 5 + b) * N + nn);
+        if (P.iE >= 0) oE[b - 1] = ldc<R>(gout + (P.iE * 5 + b) * N + nn);
+      }
+      if (useF) oF[b - 1] = ldc<R>(gout + (P.iF * 5 + b) * N + nn);
     }
-    if (nl == 0) continue;
-    R sB = R(0), sF = R(0);
-    if constexpr (NS > 0) {
-      TG* gout = (TG*)Ip->g[cur ^ 1];
-      const bool useB = (t == T_SOLID_D) && P.useB;
-      const bool useF = P.useF != 0;
 #pragma unroll
-      for (int b = 1; b < 5; ++b) {
-        const int nn = nbx[b - 1];
-        if (nn < 0) continue;
-        // the population that left nn toward this node was bounced into slot b of nn
-        if (useB) {
-          const int iB = P.iB;
-          const R Ja = rp<R>(P).Ja[iB], sh = Ja * rp<R>(P).shift_c[iB];
-          TG* slot = gout + (iB * 5 + b) * N + nn;
-          const R out = ldc<R>(slot) + sh;
-          const R kap = rp<R>(P).k2 / (R(2) * Ja);
-          const R bk = out * (R(1) - kap) / (R(1) + kap);
-          const R q = out - bk;
-          st<TG, R>(slot, bk - sh);
-          sB += q;
-          if (P.iE >= 0) {
-            TG* se = gout + (P.iE * 5 + b) * N + nn;
-            st<TG, R>(se, ldc<R>(se) + q);
-          }
-        }
-        if (useF) {
-          const int iF = P.iF;
-          const R Ja = rp<R>(P).Ja[iF], sh = Ja * rp<R>(P).shift_c[iF];
-          TG* slot = gout + (iF * 5 + b) * N + nn;
-          const R out = ldc<R>(slot) + sh;
-          const R kap = rp<R>(P).k4 / (R(2) * Ja);
-          const R bk = (out * (R(1) - kap) + rp<R>(P).k4 * rp<R>(P).C_F_sat) / (R(1) + kap);
-          st<TG, R>(slot, bk - sh);
-          sF += out - bk;
-        }
+    for (int b = 1; b < 5; ++b) {
+      const int nn = nbx[b - 1];
+      if (nn < 0) continue;
+      if (useB) {
+        const int iB = P.iB;
+        const R Ja = rp<R>(P).Ja[iB], sh = Ja * rp<R>(P).shift_c[iB];
+        const R out = oB[b - 1] + sh;
+        const R kap = rp<R>(P).k2 / (R(2) * Ja);
+        const R bk = out * (R(1) - kap) / (R(1) + kap);
+        const R q = out - bk;
+        st<TG, R>(gout + (iB * 5 + b) * N + nn, bk - sh);
+        sB += q;
+        if (P.iE >= 0) st<TG, R>(gout + (P.iE * 5 + b) * N + nn, oE[b - 1] + q);
+      }
+      if (useF) {
+        const int iF = P.iF;
+        const R Ja = rp<R>(P).Ja[iF], sh = Ja * rp<R>(P).shift_c[iF];
+        const R out = oF[b - 1] + sh;
+        const R kap = rp<R>(P).k4 / (R(2) * Ja);
+        const R bk = (out * (R(1) - kap) + rp<R>(P).k4 * rp<R>(P).C_F_sat) / (R(1) + kap);
+        st<TG, R>(gout + (iF * 5 + b) * N + nn, bk - sh);
+        sF += out - bk;
       }
     }
-    double VD = Ip->V[node], VF = Ip->V[N + node];
-    // volumes accumulate in FP64: per-step increments are far below FP32 resolution of V
-    if (t == T_SOLID_D) VD = VD - P.Vbar_D * double(sB);   // Eq. 33
-    VF = VF + P.Vbar_F * double(sF);                        // Eq. 35 (precipitation adds volume)
-    if (VD < 0.0) VD = 0.0;
-    const double total = VD + VF;
-    int code = EV_NONE;
-    if (total <= 0.0) {
-      VD = 0.0;
-      VF = 0.0;
-      code = EV_DISSOLVE;
-    } else {
-      tnew[node] = VD > 0.0 ? T_SOLID_D : T_SOLID_F;
-      if (total >= P.V_split) {
-        const double excess = total - 1.0;
-        VF = VF - excess;
-        const unsigned long long key = P.seed ^ (step << 40) ^ (unsigned long long)node;
-        const int pick = int(splitmix64(key) % (unsigned long long)nl);
-        code = EV_OVERFLOW | (dirs[pick] << 4);
-        Ip->xs[node] = excess;
-      }
+  }
+  // volumes accumulate in FP64: per-step increments are far below FP32 resolution of V
+  if (t == T_SOLID_D) VD = VD - P.Vbar_D * double(sB);   // Eq. 33
+  VF = VF + P.Vbar_F * double(sF);                        // Eq. 35 (precipitation adds volume)
+  if (VD < 0.0) VD = 0.0;
+  const double total = VD + VF;
+  int code = EV_NONE;
+  if (total <= 0.0) {
+    VD = 0.0;
+    VF = 0.0;
+    code = EV_DISSOLVE;
+  } else {
+    tnew[node] = VD > 0.0 ? T_SOLID_D : T_SOLID_F;
+    if (total >= P.V_split) {
+      const double excess = total - 1.0;
+      VF = VF - excess;
+      const unsigned long long key = P.seed ^ (step << 40) ^ (unsigned long long)node;
+      const int pick = int(splitmix64(key) % (unsigned long long)nl);
+      code = EV_OVERFLOW | (dirs[pick] << 4);
+      Ip->xs[node] = excess;
     }
-    Ip->V[node] = VD;
-    Ip->V[N + node] = VF;
-    if (code != EV_NONE) {
-      Ip->evt[node] = (uint8_t)code;
-      const unsigned long long slot = atomicAdd(&Ip->scal[S_NEVENT], 1ULL);
-      if (slot < (unsigned long long)Ip->evcap)
-        Ip->evlist[slot] = node;
-      else
-        atomicOr(&Ip->scal[S_STATUS], (unsigned long long)ST_EVOVERFLOW);
+  }
+  V[node] = VD;
+  V[N + node] = VF;
+  if (code != EV_NONE) {
+    Ip->evt[node] = (uint8_t)code;
+    const unsigned long long slot = atomicAdd(&Ip->scal[S_NEVENT], 1ULL);
+    if (slot < (unsigned long long)Ip->evcap)
+      Ip->evlist[slot] = node;
+    else
+      atomicOr(&Ip->scal[S_STATUS], (unsigned long long)ST_EVOVERFLOW);
+  }
+}
+
+template <class TF, class TG, class R, int NS>
+__global__ void __launch_bounds__(NTHREADS) k_vop(const DevInst* __restrict__ insts, int ninst) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int ws = (gridDim.x * blockDim.x) >> 5;
+  for (int ii = 0; ii < ninst; ++ii) {
+    const DevInst* Ip = insts + ii;
+    const unsigned long long step = Ip->scal[S_STEP];
+    if (step >= Ip->scal[S_LIMIT]) continue;   // frozen instance
+    const int N = (int)Ip->N;
+    const int nw = (N + 31) >> 5;
+    const int cur = int(step & 1ULL);
+    for (int w = w0; w < nw; w += ws) {
+      const unsigned m = Ip->vmask[w];        // the same word for the whole warp
+      if (m == 0u) continue;
+      __syncwarp();
+      if (lane == 0) Ip->vmask[w] = 0u;
+      if (m & (1u << lane)) vop_node<TF, TG, R, NS>(Ip, Ip->P, N, cur, step, (w << 5) + lane);
     }
   }
 }

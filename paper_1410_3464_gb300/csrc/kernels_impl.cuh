@@ -65,10 +65,20 @@ void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* in
         <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, unused);
   }
 }
-template <class SH, int NS>
-void vop_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
-  if (ntiles <= 0) return;
-  k_vop<SH, KTF, KTG, KR, NS><<<ntiles, NTHREADS, 0, s>>>(tiles, ntiles, insts);
+// Grid over the interface bitmap words of the largest member (one word per
+// warp), capped at 8 resident blocks per SM (warps then stride).
+template <int NS>
+void vop_l(cudaStream_t s, int ninst, const DevInst* insts, long long max_words) {
+  if (ninst <= 0 || max_words <= 0) return;
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cap = (sms > 0 ? sms : 1) * 8;
+  }
+  const long long need = (max_words * 32 + NTHREADS - 1) / NTHREADS;
+  k_vop<KTF, KTG, KR, NS><<<int(need < cap ? need : cap), NTHREADS, 0, s>>>(insts, ninst);
 }
 template <int NS>
 void amend_l(cudaStream_t s, int ninst, const DevInst* insts) {
@@ -101,11 +111,11 @@ constexpr Launchers make() {
     return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>},
                      {&bulk_tma_l<ShapeA, 0, NS, 2>, &bulk_tma_l<ShapeB, 1, NS, 2>},
                      {&bulk_tma_l<ShapeA, 0, NS, 1>, &bulk_tma_l<ShapeB, 1, NS, 1>},
-                     {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>},
+                     &vop_l<NS>,
                      &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
   } else {
     return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>}, {nullptr, nullptr}, {nullptr, nullptr},
-                     {&vop_l<ShapeA, NS>, &vop_l<ShapeB, NS>},
+                     &vop_l<NS>,
                      &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
   }
 }

@@ -3,6 +3,7 @@
 // capture of whole steps, field read-out and batches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -60,6 +61,7 @@ struct Stepper {
   int fix_staged = -1;
   bool staged_ok = false;                  // every instance has TMA descriptors
   const DevParams* single = nullptr;       // host parameters of a one-simulation stepper
+  long long max_words = 0;                 // largest interface bitmap of the instances
   bool tuned = false;                      // variant chosen (by timing or by the caller)
   GraphCache graphs;
   double trial_ms[NSHAPES][NSTAGING] = {};
@@ -352,7 +354,7 @@ void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int staged, int
       st.L->bulk_tma[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
     else
       st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
-    st.L->vop[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
+    st.L->vop(s, st.ninst, st.d, st.max_words);
     st.L->amend(s, st.ninst, st.d);
   }
 }
@@ -635,6 +637,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   AL(I.xs, (size_t)N * sizeof(double));
   AL(I.evlist, (size_t)N * 2 * sizeof(int));
   AL(I.claim, (size_t)N * sizeof(int));
+  AL(I.vmask, (size_t)((N + 31) / 32) * sizeof(unsigned));
   AL(I.scal, S_NSCAL * sizeof(unsigned long long));
   AL(h->d, sizeof(DevInst));
   {
@@ -659,6 +662,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
     if (e == cudaSuccess && dc) e = cudaMemcpyAsync(dc, conc, N * ns * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.evt, 0, (size_t)N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.claim, 0, (size_t)N * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.vmask, 0, (size_t)((N + 31) / 32) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.scal, 0, S_NSCAL * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.scal + S_LIMIT, 0xff, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.f[1], 0, (size_t)N * 18 * fsize(p->precision), s);
@@ -735,6 +739,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   h->run.d = h->d;
   h->run.ninst = 1;
   h->run.dims.assign(1, {p->nx, p->ny});
+  h->run.max_words = (N + 31) / 32;
   h->run.single = &h->h.P;
   choose(h->run);
   {
@@ -795,7 +800,7 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
     else
       h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
     cudaEventRecord(ev[1], s);
-    h->L->vop[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
+    h->L->vop(s, 1, h->d, h->run.max_words);
     cudaEventRecord(ev[2], s);
     h->L->amend(s, 1, h->d);
     cudaEventRecord(ev[3], s);
@@ -835,10 +840,11 @@ pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes)
   const uint64_t N = (uint64_t)p->nx * (uint64_t)p->ny;
   const uint64_t per = 2 * 18 * fsize(p->precision) + 2 * 5 * (uint64_t)p->n_species * gsize(p->precision) +
                        2 /*types*/ + 16 /*V*/ + 1 /*events*/ + 8 /*excess*/ + 8 /*event lists*/ + 4 /*claims*/;
+  const uint64_t vmask_bytes = ((N + 31) / 32) * 4;
   uint64_t tiles = 0;
   for (int sh = 0; sh < NSHAPES; ++sh)
     tiles += ((uint64_t)(p->nx + SHAPE_TX[sh] - 1) / SHAPE_TX[sh]) * ((uint64_t)(p->ny + SHAPE_TY[sh] - 1) / SHAPE_TY[sh]);
-  *bytes = N * per + tiles * sizeof(Tile) + sizeof(DevInst) + S_NSCAL * 8 + 12 * 16;
+  *bytes = N * per + vmask_bytes + tiles * sizeof(Tile) + sizeof(DevInst) + S_NSCAL * 8 + 13 * 16;
   return PSLBM_OK;
 }
 
@@ -1032,6 +1038,7 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
     b->members.push_back(members[i]);
     di.push_back(members[i]->h);
     b->run.dims.push_back({members[i]->p.nx, members[i]->p.ny});
+    b->run.max_words = std::max(b->run.max_words, (members[i]->N + 31) / 32);
   }
   cudaStream_t s = lib_stream();
   cudaError_t e = cudaMalloc(&b->d, di.size() * sizeof(DevInst));

@@ -2,14 +2,19 @@
 
     python -m paper_1410_3464_gb300.throughput --workload large --steps 300
         porous discs 4096x2048 (seed 1), one simulation
+    python -m paper_1410_3464_gb300.throughput --workload plain --steps 2000
+        the plain-method scene (128x64, one grain, one bubble, 2 species), FP64
+    python -m paper_1410_3464_gb300.throughput --workload porous-fp64 --steps 300
+        porous discs 1024x512 (seed 1) on the FP64 path
     python -m paper_1410_3464_gb300.throughput --workload batch --instances 256 --steps 300
         independent porous geometries (seed 4), sides log-uniform 128-1024
         (multiples of 16), porosity U[0.4, 0.8], rates log-uniform 1e-6-1e-1,
         stepped together as one batch (one launch per kernel per step over the
         packed tile list, CUDA graphs of up to 32 steps)
 
-Both working sets exceed the 129 MB L2 by an order of magnitude, so no flush
-is needed between steps.  The step count is timed with CUDA events on the
+The large-lattice and batch working sets exceed the 129 MB L2 by an order of
+magnitude, so no flush is needed between steps; the plain scene (3.7 MB in
+FP64) lives in L2 and is launch-bound, and its figure is MLUPS only.  The step count is timed with CUDA events on the
 library stream after the variant autotuning and a warm-up; the JSON line
 gives MLUPS over all nodes, the algorithmic bytes of the bulk kernel (fluid
 nodes x 144 B + liquid nodes x 120 B + 2 B per node for FP32 with three
@@ -56,14 +61,15 @@ def timed(run_steps, steps, stream):
     return a.elapsed_time(b) * 1e-3
 
 
-def large(args):
+def large(args, precision=pslbm.FP32, scene=None, name=None):
     import torch
     stream = torch.cuda.ExternalStream(pslbm.get_stream())
     t0 = time.time()
-    sc = inputs.porous_discs(nx=args.nx, ny=args.ny, seed=args.seed)
+    sc = scene if scene is not None else inputs.porous_discs(nx=args.nx, ny=args.ny, seed=args.seed)
     gen_s = time.time() - t0
+    fs = 8 if precision == pslbm.FP64 else 4
     with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
-                          precision=pslbm.FP32) as s:
+                          precision=precision) as s:
         s.step(40)                       # autotuning (24 steps) and warm-up
         s.sync()
         el = timed(s.step, args.steps, stream)
@@ -71,11 +77,11 @@ def large(args):
         types = s.read(pslbm.F_TYPE)["type"]
         tx, ty, _ = s.tile_shape()
         staged = s.staging()[0]
-    nbytes, nf, nl = step_bytes(types, sc["params"]["n_species"])
-    N = args.nx * args.ny
+    nbytes, nf, nl = step_bytes(types, sc["params"]["n_species"], fs=fs, gs=fs)
+    N = types.size
     pk, src = peak_gbs()
     gbs = nbytes * args.steps / el / 1e9
-    return dict(workload=f"porous discs {args.nx}x{args.ny} (seed {args.seed}), FP32, one simulation",
+    return dict(workload=name or f"porous discs {args.nx}x{args.ny} (seed {args.seed}), FP32, one simulation",
                 nodes=N, fluid_nodes=nf, liquid_nodes=nl, steps=args.steps, seconds=el,
                 mlups=N * args.steps / el / 1e6, ms_per_step=1e3 * el / args.steps,
                 bulk_bytes_per_step=nbytes, step_gbs=gbs, peak_gbs=pk, peak_source=src, frac_of_peak=gbs / pk,
@@ -124,7 +130,7 @@ def batch(args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", choices=["large", "batch"], default="large")
+    ap.add_argument("--workload", choices=["large", "batch", "plain", "porous-fp64"], default="large")
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--instances", type=int, default=256)
@@ -133,7 +139,17 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.seed is None:
         args.seed = 1 if args.workload == "large" else 4
-    out = large(args) if args.workload == "large" else batch(args)
+    if args.workload == "large":
+        out = large(args)
+    elif args.workload == "batch":
+        out = batch(args)
+    elif args.workload == "plain":
+        out = large(args, precision=pslbm.FP64, scene=inputs.bubble_grain(),
+                    name="plain-method scene 128x64 (one D(s) grain r=12, one bubble r=10, species A, B), FP64")
+    else:
+        out = large(args, precision=pslbm.FP64, scene=inputs.porous_discs(nx=1024, ny=512, seed=1),
+                    name="porous discs 1024x512 (seed 1), FP64, one simulation")
+    out["precision"] = "fp64" if args.workload in ("plain", "porous-fp64") else "fp32"
     print(json.dumps(out), flush=True)
 
 
