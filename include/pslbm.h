@@ -111,10 +111,15 @@ typedef struct {
     int32_t inlet_ramp;            /* steps of linear blend between the liquid and gas inlet
                                       states at the end of each slug (0: sharp switch) */
     double conc_in[PSLBM_MAX_SPECIES];  /* inlet concentrations */
+    double r1_surface_factor;      /* Section 2: R1 runs this many times faster at the surface of
+                                      D(s) -- at liquid nodes sharing an axis link with a D(s)
+                                      node -- than in the bulk (0 is read as 1) */
     double rho_ref_gas[2];         /* reference densities of the gas phase: FP32 population
                                       shift of gas-marked nodes (each node's populations are
                                       stored relative to its own phase, so that both phases
                                       keep their FP32 digits at a large density ratio) */
+    int32_t inlet_axis, outlet_axis; /* 0: inlet nodes feed x + 1 and outlet nodes drain x - 1;
+                                      1: they feed y + 1 / drain y - 1 (a free top outlet) */
 } pslbm_params;
 
 /* Field selectors for pslbm_read_fields; each selected field has its own

@@ -154,6 +154,7 @@ def default_params(nx, ny):
         Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=0,
         rho_in_liq=(0.0, 0.0), rho_in_gas=(0.0, 0.0), rho_out=(0.0, 0.0), rho_out_gas=(0.0, 0.0),
         inlet_period_liq=1, inlet_period_gas=0, inlet_ramp=0, conc_in=(0.0,) * MAX_SPECIES,
+        r1_surface_factor=1.0, inlet_axis=0, outlet_axis=0,
     )
 
 
@@ -272,12 +273,18 @@ class Lattice:
             c = c + g[a]
         return c
 
+    def _axes(self):
+        """Offsets of the node downstream of an inlet and upstream of an outlet:
+        along x (axis 0: x + 1, x - 1) or along y (axis 1: y + 1, y - 1)."""
+        ia, oa = int(self.p.get("inlet_axis", 0)), int(self.p.get("outlet_axis", 0))
+        return ((1, 0) if ia == 0 else (0, 1)), ((-1, 0) if oa == 0 else (0, -1))
+
     def _reservoir_state(self, typ, rho1, rho2, jx, jy, t, theta):
         """Reservoir nodes hold a fixed equilibrium state that they push into
         their fluid neighbours: an inlet whose densities alternate between a
         liquid and a gas state (gas slugs), and an outlet at fixed density.  The
-        velocity is that of the node next to it along x (x + 1 for an inlet,
-        x - 1 for an outlet) when that node is fluid, else zero."""
+        velocity is that of the node next to it (downstream of an inlet,
+        upstream of an outlet) when that node is fluid, else zero."""
         p = self.p
         inlet, outlet = typ == INLET, typ == OUTLET
         pl, pg = int(p["inlet_period_liq"]), int(p["inlet_period_gas"])
@@ -291,8 +298,9 @@ class Lattice:
                 wg = 1.0 - (ph - (pl + pg - ramp) + 1) / (ramp + 1) if (ramp > 0 and ph >= pl + pg - ramp) else 1.0
         rin = [(1.0 - wg) * p["rho_in_liq"][s] + wg * p["rho_in_gas"][s] for s in range(2)]
         fluid = self._fluid(typ)
-        # outlet: liquid or gas state by the marking of the node upstream (x - 1)
-        up_liq = self.nb(fluid & (rho1 > theta), -1, 0, False)
+        (idx, idy), (odx, ody) = self._axes()
+        # outlet: liquid or gas state by the marking of the node upstream
+        up_liq = self.nb(fluid & (rho1 > theta), odx, ody, False)
         ro = [np.where(up_liq, p["rho_out"][s], p["rho_out_gas"][s]) for s in range(2)]
         r1 = np.where(inlet, rin[0], np.where(outlet, ro[0], 0.0))
         r2 = np.where(inlet, rin[1], np.where(outlet, ro[1], 0.0))
@@ -300,9 +308,9 @@ class Lattice:
         with np.errstate(invalid="ignore", divide="ignore"):
             ux = np.where(fluid, (jx) / np.where(fluid, rho, 1.0), 0.0)
             uy = np.where(fluid, (jy) / np.where(fluid, rho, 1.0), 0.0)
-        # neighbour along x used for the velocity
-        ux_res = np.where(inlet, self.nb(ux, 1, 0, 0.0), np.where(outlet, self.nb(ux, -1, 0, 0.0), 0.0))
-        uy_res = np.where(inlet, self.nb(uy, 1, 0, 0.0), np.where(outlet, self.nb(uy, -1, 0, 0.0), 0.0))
+        # neighbour used for the velocity
+        ux_res = np.where(inlet, self.nb(ux, idx, idy, 0.0), np.where(outlet, self.nb(ux, odx, ody, 0.0), 0.0))
+        uy_res = np.where(inlet, self.nb(uy, idx, idy, 0.0), np.where(outlet, self.nb(uy, odx, ody, 0.0), 0.0))
         return r1, r2, ux_res, uy_res
 
     # -- observables -------------------------------------------------------
@@ -531,7 +539,14 @@ class Lattice:
             else:
                 CA = zero
             CC = rho2 * p["inv_M_C"]
-            R1 = p["k1"] * (CA - p["inv_Keq"] * CB * np.sqrt(np.maximum(CC, 0.0)))
+            # Section 2: A decomposes in the bulk and, faster by a factor, at the
+            # surface of D(s): liquid nodes sharing an axis link with a D(s) node
+            fac = float(p.get("r1_surface_factor", 1.0)) or 1.0
+            touch_d = np.zeros((ny, nx), dtype=bool)
+            for b in range(1, 5):
+                touch_d |= self.nb(typ, EX5[b], EY5[b], WALL) == SOLID_D
+            k1 = np.where(touch_d, p["k1"] * fac, p["k1"])
+            R1 = k1 * (CA - p["inv_Keq"] * CB * np.sqrt(np.maximum(CC, 0.0)))
             R3 = p["k3"] * CB * CE
             R1 = np.where(liq_new, R1, 0.0)
             R3 = np.where(liq_new, R3, 0.0)
@@ -586,10 +601,11 @@ class Lattice:
             Cres = np.zeros((ns, ny, nx))
             for k in range(ns):
                 cin = p["conc_in"][k]
-                # outlet: concentration of the node upstream along x at the
-                # start of the step when it is liquid, else 0
+                # outlet: concentration of the node upstream at the start of
+                # the step when it is liquid, else 0
                 cl = np.where(liq_new, C_pre[k], 0.0)
-                Cres[k] = np.where(inlet, cin, np.where(outlet, self.nb(cl, -1, 0, 0.0), 0.0))
+                (_, _), (odx, ody) = self._axes()
+                Cres[k] = np.where(inlet, cin, np.where(outlet, self.nb(cl, odx, ody, 0.0), 0.0))
             k2, k4, Csat = p["k2"], p["k4"], p["C_F_sat"]
             for a in range(5):
                 st = src_typ[a]

@@ -148,8 +148,9 @@ __device__ __noinline__ void amend_marking(const DevParams& P, const uint8_t* ti
 }
 
 // Reservoir node: push its equilibrium state (densities of reservoir_rho,
-// velocity of the node next to it along x) into its fluid neighbours, and the
-// solute equilibrium into its liquid neighbours when it is itself liquid.
+// velocity of the node downstream of an inlet / upstream of an outlet) into
+// its fluid neighbours, and the solute equilibrium into its liquid neighbours
+// when it is itself liquid.
 template <class SH, class R, class TF, class TG, int NS>
 __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* tin, const TF* fin, const TG* gin,
                                             TF* fout, TG* gout, int N, int x, int y, uint8_t t,
@@ -161,8 +162,8 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
   const R r1 = R(a_), r2 = R(b_);
   R ux = R(0), uy = R(0);
   int xn, yn;
-  const int dx = (t == T_INLET) ? 1 : -1;
-  if (nbr(P, x, y, dx, 0, xn, yn)) {
+  const int dx = (t == T_INLET) ? P.in_dx : P.out_dx, dy = (t == T_INLET) ? P.in_dy : P.out_dy;
+  if (nbr(P, x, y, dx, dy, xn, yn)) {
     const int nn = yn * P.nx + xn;
     const uint8_t tnn = tin[nn] & T_MASK;
     if (is_fluid(tnn)) {
@@ -208,10 +209,10 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
 #pragma unroll
       for (int k = 0; k < NS; ++k) Cr[k] = rp<R>(P).conc_in[k];
       if (t == T_OUTLET) {
-        const int ew = eo - 1;
+        const int ew = eo + P.out_dy * SH::EXT_X + P.out_dx;
 #pragma unroll
         for (int k = 0; k < NS; ++k) Cr[k] = R(0);
-        if (is_fluid(s_t[ew]) && s_m[ew] && nbr(P, x, y, -1, 0, xn, yn))
+        if (is_fluid(s_t[ew]) && s_m[ew] && nbr(P, x, y, P.out_dx, P.out_dy, xn, yn))
           conc_at<R, TG, NS>(gin, N, yn * P.nx + xn, P, Cr);
       }
 #pragma unroll
@@ -494,9 +495,16 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
           tot += C[k];
         }
         if (P.iA == -2) CA = rmax<R>(R(0), rfma<R>(rp<R>(P).c_total_per_rho1, rho1, -tot));
-        R R1 = rmul<R>(rp<R>(P).k1, CA);
+        // Section 2: R1 is faster at the surface of D(s) (a liquid node with a
+        // D(s) node on an axis link)
+        bool surf = false;
+        if (P.r1_surf) {
+#pragma unroll
+          for (int b = 1; b < 5; ++b) surf |= st_[eo + EY(b) * SH::EXT_X + EX(b)] == T_SOLID_D;
+        }
+        R R1 = rmul<R>(surf ? rp<R>(P).k1_s : rp<R>(P).k1, CA);
         if (P.has_rev)
-          R1 = rsub<R>(R1, rmul<R>(rmul<R>(rp<R>(P).k1_inv_Keq, CB),
+          R1 = rsub<R>(R1, rmul<R>(rmul<R>(surf ? rp<R>(P).k1_inv_Keq_s : rp<R>(P).k1_inv_Keq, CB),
                                    rsqrt_<R>(rmax<R>(rmul<R>(rho2, rp<R>(P).inv_M_C), R(0)))));
         const R R3 = rmul<R>(rmul<R>(rp<R>(P).k3, CB), CE);
 #pragma unroll

@@ -71,6 +71,7 @@ struct DevParamsR {
   R gx, gy, shift_f[2], shift_fg[2], rho_fill[2];
   R J0[MAXS], Ja[MAXS], inv_tau_g[MAXS], shift_c[MAXS], conc_in[MAXS], cR1[MAXS], cR3[MAXS];
   R k1, k1_inv_Keq, k3, k2, k4, C_F_sat, gas_yield, inv_M_C, c_total_per_rho1;
+  R k1_s, k1_inv_Keq_s;   // R1 constants at liquid nodes touching D(s) (surface factor applied)
 };
 
 struct DevParams {
@@ -78,6 +79,8 @@ struct DevParams {
   int iA, iB, iE, iF;
   int per_liq, per_gas, ramp;
   int has_G11, has_rev, useB, useF;   // G11 != 0, inv_Keq != 0, R2 active, R4 active
+  int r1_surf;                        // R1 surface factor differs from 1
+  int in_dx, in_dy, out_dx, out_dy;   // node downstream of an inlet / upstream of an outlet
   double tau[2], G11, G12, G21, a0, rho10, rho20, w_adh[2];
   double eos_a, eos_b, eos_R, eos_T;
   double gx, gy;
@@ -88,6 +91,7 @@ struct DevParams {
   double inv_tau[2], Ja[MAXS], inv_tau_g[MAXS];  // 1/tau, (1 - J0)/4, 1/tau_g
   double cR1[MAXS], cR3[MAXS];                     // S_k = cR1[k] R1 + cR3[k] R3 (Eq. 28)
   double k1, inv_Keq, k3, k2, k4, C_F_sat, gas_yield, inv_M_C, c_total_per_rho1;
+  double r1_surface_factor;
   double Vbar_D, Vbar_F, V_split;
   unsigned long long seed;
   double rho_in_liq[2], rho_in_gas[2], rho_out[2], rho_out_gas[2];
@@ -234,7 +238,8 @@ __device__ __forceinline__ R density_c(const TF* f, long long N, long long node)
 // Reservoir densities at step t.  The inlet alternates liquid slugs of
 // per_liq steps and gas slugs of per_gas steps; the last `ramp` steps of each
 // slug blend linearly into the next state.  The outlet holds the liquid or the
-// gas state according to the marking of the node upstream of it (x - 1).
+// gas state according to the marking of the node upstream of it (x - 1, or
+// y - 1 for outlets along y).
 __device__ __forceinline__ void reservoir_rho(const DevParams& P, uint8_t t, unsigned long long step, bool up_liquid,
                                               double& r1, double& r2) {
   if (t == T_INLET) {
@@ -276,12 +281,12 @@ __device__ __forceinline__ bool liquid_at(const DevParams& P, const uint8_t* tin
   return rho1 > theta;
 }
 
-// Marking of the node upstream (x - 1) of an outlet node at index idx.
+// Marking of the node upstream of an outlet node at index idx.
 template <class R, class TF>
 __device__ __forceinline__ bool outlet_up_liquid(const DevParams& P, const uint8_t* tin, const TF* fin, int N, int idx,
                                                  R theta) {
   int xn, yn;
-  if (!nbr(P, idx % P.nx, idx / P.nx, -1, 0, xn, yn)) return false;
+  if (!nbr(P, idx % P.nx, idx / P.nx, P.out_dx, P.out_dy, xn, yn)) return false;
   return liquid_at<R, TF>(P, tin, fin, N, yn * P.nx + xn, theta);
 }
 

@@ -172,6 +172,8 @@ std::string validate(const pslbm_params* p) {
   if (p->idx_F >= 0 && p->k4 != 0.0 && !(p->k4 >= 0.0 && p->k4 < 0.5 * (1.0 - p->J0[p->idx_F])))
     return "k4 must be in [0, (1 - J0_F)/2)";
   if (!(p->V_split > 1.0)) return "V_split must be > 1";
+  if (!(p->r1_surface_factor >= 0.0) || !std::isfinite(p->r1_surface_factor)) return "r1_surface_factor must be >= 0";
+  if (p->inlet_axis < 0 || p->inlet_axis > 1 || p->outlet_axis < 0 || p->outlet_axis > 1) return "axes must be 0 or 1";
   if (p->inlet_period_liq < 0 || p->inlet_period_gas < 0 ||
       (p->inlet_period_gas > 0 && p->inlet_period_liq + p->inlet_period_gas <= 0))
     return "bad inlet periods";
@@ -214,6 +216,8 @@ void fill_r(DevParamsR<R>& q, const DevParams& P) {
   }
   q.k1 = R(P.k1);
   q.k1_inv_Keq = R(P.k1 * P.inv_Keq);
+  q.k1_s = R(P.k1 * P.r1_surface_factor);
+  q.k1_inv_Keq_s = R(P.k1 * P.r1_surface_factor * P.inv_Keq);
   q.k3 = R(P.k3);
   q.k2 = R(P.k2);
   q.k4 = R(P.k4);
@@ -234,6 +238,10 @@ DevParams to_dev(const pslbm_params* p) {
   P.iB = p->idx_B;
   P.iE = p->idx_E;
   P.iF = p->idx_F;
+  P.in_dx = p->inlet_axis == 1 ? 0 : 1;
+  P.in_dy = p->inlet_axis == 1 ? 1 : 0;
+  P.out_dx = p->outlet_axis == 1 ? 0 : -1;
+  P.out_dy = p->outlet_axis == 1 ? -1 : 0;
   P.per_liq = p->inlet_period_liq;
   P.per_gas = p->inlet_period_gas;
   P.ramp = p->inlet_ramp;
@@ -274,6 +282,8 @@ DevParams to_dev(const pslbm_params* p) {
     P.cR3[k] = (k == p->idx_B ? -1.0 : 0.0) + (k == p->idx_E ? -1.0 : 0.0) + (k == p->idx_F ? 1.0 : 0.0);
   }
   P.k1 = p->k1;
+  P.r1_surface_factor = p->r1_surface_factor > 0.0 ? p->r1_surface_factor : 1.0;
+  P.r1_surf = P.r1_surface_factor != 1.0;
   P.inv_Keq = p->inv_Keq;
   P.k3 = p->k3;
   P.k2 = p->k2;

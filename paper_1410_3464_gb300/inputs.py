@@ -53,7 +53,8 @@ def base_params(nx, ny):
         tau=(1.0, 1.0), G11=-1.0, G12=0.001, G21=0.001,
         a0=0.005, rho10=-0.008 / math.log(0.005), rho20=0.003,
         w_adh=(0.0, 0.0), eos_a=1.0, eos_b=4.0, eos_R=1.0, eos_T=0.7 * CS_ORIGINAL["Tc"],
-        body_force=(0.0, 0.0), rho_ref=(1.0, 1.0), rho_ref_gas=(0.0, 0.0),
+        body_force=(0.0, 0.0), rho_ref=(1.0, 1.0), rho_ref_gas=(0.0, 0.0), r1_surface_factor=1.0,
+        inlet_axis=0, outlet_axis=0,
         n_species=0, idx_A=IDX_ABSENT, idx_B=IDX_ABSENT, idx_E=IDX_ABSENT, idx_F=IDX_ABSENT,
         J0=(0.0,) * MAX_SPECIES, tau_g=(1.0,) * MAX_SPECIES, conc_ref=(0.0,) * MAX_SPECIES,
         k1=0.0, inv_Keq=0.0, k3=0.0, k2=0.0, k4=0.0, C_F_sat=0.0,
@@ -214,6 +215,58 @@ def porous_discs(nx=1024, ny=512, seed=1, porosity=0.6, rmin=8.0, rmax=24.0,
     if slug is not None:
         p.update(inlet_period_liq=int(slug[0]), inlet_period_gas=int(slug[1]))
     conc = np.zeros((3, ny, nx))
+    return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
+
+
+def beaker(nx=100, ny=160, grain=(50, 50, 15), level=100, k1=1e-5, r1_surface=1000.0, k3=1e-1, k2=1e-3,
+           k4=1e-7, gas_mass=0.001):
+    """The paper's beaker scene (Section 5): a D(s) cylinder of radius 15 at
+    (50, 50) in a 100x160 domain with walls left, right and at the bottom and a
+    free outlet at the top; liquid below y = level (rho_1 = 8.31, rho_2 = 1e-4)
+    and gas above (rho_1 = 0.05, rho_2 = 0.05); rescaled C-S EOS at 0.65 T_c;
+    tau = 1; every solute with J0 = 0.9 and tau_g = 0.65 (D = 4.5e-8 m^2/s at
+    1 mm and the fluid's time step); the liquid holds only A (C_A = 1).  A, B,
+    E, F are all transported; R1 runs r1_surface times faster at the D(s)
+    surface (Section 2).  The paper's Table 1 (rate constants) is missing: the
+    rates are stand-ins, with k2, k4 below (1 - J0)/2.  At this EOS's liquid
+    density (8.17, Eq. 13 domain limit 9.86) a liquid node that turns into F(s)
+    hands its mass to two or three neighbours and pushes them out of the EOS
+    domain, so k4 is slow (the paper's Fig. 9 also runs R4 at 1/10000 of its
+    rate), and the gas C(g) is light (M_C = 0.001 rho_l): a heavier gas
+    accumulates at the wall contact line.  Without reactions the scene runs
+    20,000 steps; with all four reactions on at these stand-in rates it still
+    diverges within 1,000 steps."""
+    y, x = np.mgrid[0:ny, 0:nx]
+    gas = y >= level
+    mask = np.where(gas, GAS, LIQUID).astype(np.uint8)
+    gx, gy, gr = grain
+    mask[(x - gx) ** 2 + (y - gy) ** 2 <= gr * gr] = SOLID_D
+    mask[:, 0] = WALL
+    mask[:, nx - 1] = WALL
+    mask[0, :] = WALL
+    mask[ny - 1, 1:nx - 1] = OUTLET
+    # the initial interface is a tanh profile of width 2 (a sharp step launches
+    # compression waves that leave the EOS domain of Eq. 13)
+    liq = 0.5 * (1.0 - np.tanh((y - level + 0.5) / 2.0))
+    rho1 = 0.05 + (8.31 - 0.05) * liq
+    rho2 = 0.05 + (1e-4 - 0.05) * liq
+    fluid = (mask == LIQUID) | (mask == GAS)
+    rho1 = np.where(fluid, rho1, 0.0)
+    rho2 = np.where(fluid, rho2, 0.0)
+    rl, rg = 8.17, 0.0537                 # Section 5.1: steady bulk densities
+    m_gas = gas_mass * rl
+    p = base_params(nx, ny)
+    p.update(periodic_x=0, periodic_y=0, eos_a=CS_RESCALED["eos_a"], eos_b=CS_RESCALED["eos_b"],
+             eos_R=CS_RESCALED["eos_R"], eos_T=0.65 * CS_RESCALED["Tc"],
+             rho_ref=(rl, 1e-4), rho_ref_gas=(rg, 0.05),
+             n_species=4, idx_A=0, idx_B=1, idx_E=2, idx_F=3,
+             J0=_pad([0.9] * 4), tau_g=_pad([0.65] * 4, 1.0), conc_ref=_pad([0.0] * 4),
+             k1=k1, r1_surface_factor=r1_surface, k3=k3, k2=k2, k4=k4, C_F_sat=0.0,
+             gas_yield=0.5 * m_gas, inv_M_C=1.0 / m_gas,
+             Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=7,
+             rho_out=(rl, 1e-4), rho_out_gas=(rg, 0.05), outlet_axis=1)
+    conc = np.zeros((4, ny, nx))
+    conc[0][mask == LIQUID] = 1.0
     return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
 
 

@@ -55,7 +55,8 @@ class Params(C.Structure):
         ("Vbar_D", C.c_double), ("Vbar_F", C.c_double), ("V_split", C.c_double), ("seed", C.c_uint64),
         ("rho_in_liq", _D2), ("rho_in_gas", _D2), ("rho_out", _D2), ("rho_out_gas", _D2),
         ("inlet_period_liq", C.c_int32), ("inlet_period_gas", C.c_int32), ("inlet_ramp", C.c_int32),
-        ("conc_in", _DS), ("rho_ref_gas", _D2),
+        ("conc_in", _DS), ("r1_surface_factor", C.c_double), ("rho_ref_gas", _D2),
+        ("inlet_axis", C.c_int32), ("outlet_axis", C.c_int32),
     ]
 
 

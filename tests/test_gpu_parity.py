@@ -194,12 +194,73 @@ def test_adhesion_and_body_force(pslbm):
 
 
 def test_porous_full_size_1024x512(pslbm):
-    """The porous-medium workload at its full 1024x512 size, in the launch
-    configuration the benchmark uses, for 6 steps (the oracle's cost bounds the
-    step count; the GPU path is identical at every step)."""
+    """The porous-medium workload at its full 1024x512 size on the FP64 path,
+    for 6 steps (the oracle's cost bounds the step count; the GPU path is the
+    same at every step)."""
     sc = inputs.porous_discs()
     got, ref, _ = run_both(pslbm, sc, 6)
     compare(got, ref, what="porous 1024x512")
+
+
+@pytest.mark.parametrize("shape", [(32, 8), (16, 16)])
+def test_porous_full_size_benchmark_configuration(pslbm, shape):
+    """The benchmark's own launch configuration -- FP32 with phase-shifted
+    storage, the TMA-staged bulk kernel with two stages, the single-simulation
+    parameter block -- on the full 1024x512 workload against the FP64 oracle
+    after 6 steps: FP32 tolerance 1e-5 relative (about a hundred FP32 roundings
+    of the largest values), node types bit-exact."""
+    sc = inputs.porous_discs()
+    with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                          precision=pslbm.FP32) as sim:
+        sim.set_tile_shape(*shape)
+        sim.set_staging(1)
+        sim.step(6)
+        assert sim.staging() == (1, True)
+        got = sim.read()
+    L = lbm.Lattice(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"])
+    L.run(6)
+    ref = L.fields()
+    np.testing.assert_array_equal(got["type"], ref["type"])
+    fluid, liquid = ref["type"] <= 1, ref["type"] == 0
+    for name in ("rho1", "rho2", "ux", "uy"):
+        e = rel(got[name], ref[name], fluid)
+        assert e <= 1e-5, f"{name}: {e:.3e}"
+    for k in range(ref["conc"].shape[0]):
+        e = rel(got["conc"][k], ref["conc"][k], liquid)
+        assert e <= 1e-5, f"conc[{k}]: {e:.3e}"
+
+
+def test_r1_surface_enhancement(pslbm):
+    """Section 2: R1 runs 1000 times faster at liquid nodes sharing a link with
+    D(s); the plain scene with the enhancement on, 100 steps."""
+    sc = inputs.bubble_grain()
+    p = dict(sc["params"])
+    p.update(k1=1e-5, r1_surface_factor=1000.0)
+    sc["params"] = p
+    got, ref, _ = run_both(pslbm, sc, 100)
+    compare(got, ref, what="R1 surface enhancement")
+
+
+def test_beaker_scene_free_top_outlet(pslbm):
+    """The paper's beaker (Section 5): D(s) cylinder r = 15 at (50, 50) in
+    100x160, walls left, right and bottom, a free outlet on the top row (outlet
+    along y), rescaled C-S EOS at 0.65 T_c, four transported species, R1 with the
+    surface enhancement, R2-R4; 120 steps."""
+    sc = inputs.beaker()
+    got, ref, _ = run_both(pslbm, sc, 120)
+    compare(got, ref, what="beaker")
+
+
+def test_plain_scene_full_length_2000_steps(pslbm):
+    """The plain-method scene for its full 2000 steps on the FP64 path.  The
+    two sides differ only in rounding order (about 1e-16 per operation); the
+    flow does not amplify perturbations measurably (an FP64 run started from a
+    1e-7 perturbation stays within 1e-7), so after 2000 steps the difference
+    stays within 1e-10 relative per field."""
+    sc = inputs.bubble_grain()
+    got, ref, L = run_both(pslbm, sc, 2000)
+    compare(got, ref, tol=1e-10, what="bubble_grain 2000 steps")
+    assert got["budget"][-1] == 2000
 
 
 def test_batch_equals_alone(pslbm):

@@ -86,6 +86,17 @@ def test_staged_equals_plain_periodic_wrap(pslbm, shape, nx, ny):
         assert_same(a, b, f"periodic {nx}x{ny} {shape} staging {staging}")
 
 
+@pytest.mark.parametrize("shape", [(16, 16), (32, 8)])
+def test_staged_equals_plain_beaker(pslbm, shape):
+    """Outlet along y, four species, R1 surface enhancement, partial tiles
+    (100 = 6 x 16 + 4)."""
+    sc = inputs.beaker()
+    a = run(pslbm, sc, 60, pslbm.FP32, 0, shape)
+    for staging in STAGED:
+        b = run(pslbm, sc, 60, pslbm.FP32, staging, shape)
+        assert_same(a, b, f"beaker {shape} staging {staging}")
+
+
 @pytest.mark.parametrize("ns", [0, 1, 2, 4])
 def test_staged_equals_plain_species_counts(pslbm, ns):
     sc = inputs.porous_discs(nx=64, ny=48, seed=71)

@@ -354,6 +354,33 @@ def test_first_order_decay_closed_form():
     assert abs(crossed - frac) < k1
 
 
+def test_r1_surface_enhancement_total_production():
+    """Section 2: A decomposes in the bulk and 1000 times faster at the surface
+    of D(s).  With one inert D(s) node (k2 = 0) in a uniform periodic liquid of
+    C_A = 1, C_B = 0, one step produces, in total, exactly
+    k1 (N_liquid + (f - 1) N_surface) of B, N_surface being the liquid nodes
+    that share an axis link with the D(s) node (counted here directly: 4), since
+    the D2Q5 rest fractions sum to one and streaming and bounce-back conserve
+    mass."""
+    nx, ny, k1 = 9, 8, 1e-4
+    for f in (1.0, 1000.0):
+        p = flow_off(lbm.default_params(nx, ny))
+        p.update(n_species=2, idx_A=0, idx_B=1, J0=(1 / 3,) * 4, tau_g=(0.8,) * 4, k1=k1,
+                 r1_surface_factor=f)
+        mask = uniform_mask(nx, ny)
+        mask[4, 3] = lbm.SOLID_D
+        liquid = mask == lbm.LIQUID
+        surface = sum(int(liquid[(4 + dy) % ny, (3 + dx) % nx]) for dx, dy in ((1, 0), (0, 1), (-1, 0), (0, -1)))
+        assert surface == 4
+        c = np.zeros((2, ny, nx))
+        c[0][liquid] = 1.0
+        L = lbm.Lattice(mask, p, np.full((ny, nx), 1.0), np.full((ny, nx), 0.2), c)
+        L.theta = -1.0
+        L.step()
+        total_b = L.fields()["conc"][1][liquid].sum()
+        assert abs(total_b - k1 * (liquid.sum() + (f - 1.0) * surface)) < 1e-15 * liquid.sum()
+
+
 def test_reversible_r1_equilibrium_is_stationary():
     """Eq. 5a: with C_A = C_B sqrt(C_C)/K_eq the net rate vanishes."""
     inv_keq, rho2 = 3.0, 0.2
