@@ -19,7 +19,6 @@ workload (256x128, same generator) on the host cores.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -53,17 +52,6 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_f16", "fp32_bf16"], default="fp32")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline and e2e legs")
     return ap.parse_args()
-
-
-def kernel_source_hash():
-    """Hash of the device-code sources the bulk kernels are compiled from (an
-    ncu traffic figure is only reported for a build of these same files)."""
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1410_3464_gb300", "csrc")
-    for f in ("device.cuh", "tma.cuh", "bulk.cuh", "kernels_impl.cuh", "kernels_f32.cu"):
-        h.update(f.encode())
-        h.update(open(os.path.join(d, f), "rb").read())
-    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------ clocks
@@ -172,7 +160,7 @@ def reference_arm(args):
 def ours_arm(args):
     import torch
 
-    from paper_1410_3464_gb300 import inputs, pslbm, replicas
+    from paper_1410_3464_gb300 import inputs, profile_case, pslbm, replicas
 
     ws, rank, local = replicas.env()
     replicas.init(ws)
@@ -246,7 +234,7 @@ def ours_arm(args):
         # DRAM bytes per launch from an ncu capture of the same kernel variant
         # built from the same sources (null otherwise)
         pj = json.load(open(PROFILE_JSON))
-        if pj.get("source_hash") == kernel_source_hash():
+        if pj.get("source_hash") == profile_case.kernel_source_hash():
             traffic = pj.get("traffic_per_launch", {}).get(variant)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": KERNEL_NAMES[staged], "bytes_per_launch": bytes_per_launch,

@@ -77,22 +77,94 @@ struct TileTypes {
 };
 
 template <class SH>
-__device__ __forceinline__ TileTypes load_types(const Tile* tiles, const DevInst* insts, int ti, int tid) {
+__device__ __forceinline__ TileTypes load_types(const Tile& tl, const DevParams& P, const uint8_t* tin, int tid) {
   TileTypes tt;
-  const Tile tl = tiles[ti];
-  const DevInst* Ip = insts + tl.inst;
-  const int cur = int(Ip->scal[S_STEP] & 1ULL);
-  const uint8_t* tin = Ip->type[cur];
   const int tx = tid % SH::TX, ty = tid / SH::TX;
-  tt.own = ext_type(Ip->P, tin, tl.x0, tl.y0, tx + 1, ty + 1, tt.own_idx);
+  tt.own = ext_type(P, tin, tl.x0, tl.y0, tx + 1, ty + 1, tt.own_idx);
   tt.ring = T_WALL;
   tt.ring_idx = -1;
   if (tid < SH::RING) {
     int ex, ey;
     ring_pos<SH>(tid, ex, ey);
-    tt.ring = ext_type(Ip->P, tin, tl.x0, tl.y0, ex, ey, tt.ring_idx);
+    tt.ring = ext_type(P, tin, tl.x0, tl.y0, ex, ey, tt.ring_idx);
   }
   return tt;
+}
+
+// The same for a tile of any instance of a batch (the instance's current
+// type buffer found through its step counter).
+template <class SH>
+__device__ __forceinline__ TileTypes load_types(const Tile* tiles, const DevInst* insts, int ti, int tid) {
+  const Tile tl = tiles[ti];
+  const DevInst* Ip = insts + tl.inst;
+  const int cur = int(Ip->scal[S_STEP] & 1ULL);
+  return load_types<SH>(tl, Ip->P, Ip->type[cur], tid);
+}
+
+// What one bulk launch needs of an instance: the buffers of the current step,
+// the step and the liquid threshold.  All are fixed for the launch (the step
+// counter and the threshold advance in the amendment kernel), so a launch over
+// one simulation reads them once.
+template <class TF, class TG, class R>
+struct StepView {
+  const TF* fin;
+  TF* fout;
+  const TG* gin;
+  TG* gout;
+  const uint8_t* tin;
+  uint8_t* tout;
+  unsigned* vmask;
+  unsigned long long* scal;
+  unsigned long long step;
+  int cur, N;
+  R theta;
+};
+
+template <class TF, class TG, class R>
+__device__ __forceinline__ StepView<TF, TG, R> step_view(const DevInst* Ip) {
+  StepView<TF, TG, R> v;
+  v.step = Ip->scal[S_STEP];
+  v.cur = int(v.step & 1ULL);
+  v.fin = (const TF*)Ip->f[v.cur];
+  v.fout = (TF*)Ip->f[v.cur ^ 1];
+  v.gin = (const TG*)Ip->g[v.cur];
+  v.gout = (TG*)Ip->g[v.cur ^ 1];
+  v.tin = Ip->type[v.cur];
+  v.tout = Ip->type[v.cur ^ 1];
+  v.vmask = Ip->vmask;
+  v.scal = Ip->scal;
+  v.N = (int)Ip->N;
+  v.theta = theta_of<R>(Ip);
+  return v;
+}
+
+// Per-thread maximum of rho_1 and status bits of the tiles a thread has done
+// since the last flush.
+template <class R>
+struct TileAcc {
+  R mx;
+  unsigned status;
+};
+
+// Warp reduction of the accumulators into the instance's slots: the exact
+// maximum (the atomic only when it can raise the slot) and the status bits.
+// Called by all lanes of the warp.
+template <class R>
+__device__ __forceinline__ void flush_acc(TileAcc<R>& acc, unsigned long long* scal, int cur) {
+  R m = acc.mx;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = rmax<R>(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const unsigned st = __reduce_or_sync(0xffffffffu, acc.status);
+  if ((threadIdx.x & 31) == 0) {
+    if (m > R(-1.0 / 0.0)) {
+      const unsigned long long enc = ord_enc(double(m));
+      unsigned long long* slot = &scal[S_MAX0 + (cur ^ 1)];
+      if (enc > *(volatile unsigned long long*)slot) atomicMax(slot, enc);
+    }
+    if (st) atomicOr(&scal[S_STATUS], (unsigned long long)st);
+  }
+  acc.mx = R(-1.0 / 0.0);
+  acc.status = 0;
 }
 
 // Index of the neighbour (x + dx, y + dy) with wrap (out of line: used only by
@@ -243,6 +315,25 @@ constexpr int bulk_min_blocks() {
   return sizeof(R) == 8 ? 2 : PSLBM_BULK_MINB;
 }
 
+// Shared-memory record of one ext node: psi_1, phi_1, phi_2 (zero where not
+// live) and a code of its type and liquid marking, read by a neighbour with
+// one vector load.
+template <class R>
+struct alignas(4 * sizeof(R)) Pot {
+  R ps, p1, p2, code;
+};
+constexpr int C_TYPE = 0x7, C_MARK = 1 << 3, C_FLUID = 1 << 4, C_LIVE = 1 << 5, C_RES = 1 << 6, C_MIN = 1 << 7;
+__device__ __forceinline__ int node_code(uint8_t t, bool mark) {
+  return int(t) | (mark ? C_MARK : 0) | (is_fluid(t) ? C_FLUID : 0) | (is_live(t) ? C_LIVE : 0) |
+         (is_res(t) ? C_RES : 0) | (is_mineral(t) ? C_MIN : 0);
+}
+template <class R> __device__ __forceinline__ R code_bits(int c);
+template <> __device__ __forceinline__ float code_bits<float>(int c) { return __int_as_float(c); }
+template <> __device__ __forceinline__ double code_bits<double>(int c) { return __longlong_as_double((long long)c); }
+template <class R> __device__ __forceinline__ int code_of(R v);
+template <> __device__ __forceinline__ int code_of<float>(float v) { return __float_as_int(v); }
+template <> __device__ __forceinline__ int code_of<double>(double v) { return (int)__double_as_longlong(v); }
+
 // First tile at or after ti (stride `stride`) whose instance is not frozen at
 // its step limit; ntiles if none.
 __device__ __forceinline__ int next_live(const Tile* tiles, int ntiles, const DevInst* insts, int ti, int stride) {
@@ -285,16 +376,16 @@ struct GlobalSrc {
 // cut after the streaming of Step 1).  `src` delivers the populations,
 // `after_sync` runs once the block has passed the tile's barrier (all reads of
 // the tile's staged populations are done by then), `tt` holds this tile's node
-// types on entry and the next tile's on return.  Returns true when the block
-// must stop (a bounded wait of the staged kernel gave up in some thread).
-template <class SH, class TF, class TG, class R, int NS, class Src, class AfterSync>
-__device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, const DevParams& P, const Src& src,
-                                          AfterSync after_sync,
-                                          bool waited_ok, TileTypes& tt, const Tile* tiles, int ntiles,
-                                          const DevInst* insts, int next_ti, R* sp, R* sq1, R* sq2, uint8_t* st_,
+// types on entry and the next tile's on return (`next_types(tt)` loads them).
+// The tile's maximum of rho_1 and its status bits go into `acc`.  Returns true
+// when the block must stop (a bounded wait of the staged kernel gave up in
+// some thread).
+template <class SH, class TF, class TG, class R, int NS, class Src, class AfterSync, class NextTypes>
+__device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG, R>& V, const DevParams& P,
+                                          const Src& src, AfterSync after_sync, NextTypes next_types, bool waited_ok,
+                                          TileTypes& tt, TileAcc<R>& acc, Pot<R>* spot, uint8_t* st_,
                                           uint8_t* sm_) {
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
   const int tx = tid % SH::TX, ty = tid / SH::TX;
   const int eo = (ty + 1) * SH::EXT_X + (tx + 1);
   int er = -1, rex = 0, rey = 0;
@@ -302,17 +393,16 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     ring_pos<SH>(tid, rex, rey);
     er = rey * SH::EXT_X + rex;
   }
-  const int N = (int)Ip->N;
+  const int N = V.N;
   const int nx = P.nx;
-  const unsigned long long step = Ip->scal[S_STEP];
-  const int cur = int(step & 1ULL);
-  const TF* __restrict__ fin = (const TF*)Ip->f[cur];
-  TF* __restrict__ fout = (TF*)Ip->f[cur ^ 1];
-  const TG* __restrict__ gin = (const TG*)Ip->g[cur];
-  TG* __restrict__ gout = (TG*)Ip->g[cur ^ 1];
-  const uint8_t* __restrict__ tin = Ip->type[cur];
-  uint8_t* __restrict__ tout = Ip->type[cur ^ 1];
-  const R theta = theta_of<R>(Ip);
+  const unsigned long long step = V.step;
+  const TF* __restrict__ fin = V.fin;
+  TF* __restrict__ fout = V.fout;
+  const TG* __restrict__ gin = V.gin;
+  TG* __restrict__ gout = V.gout;
+  const uint8_t* __restrict__ tin = V.tin;
+  uint8_t* __restrict__ tout = V.tout;
+  const R theta = V.theta;
   // tiles whose ring is inside the domain need no wrap arithmetic
   const bool inner = tl.x0 >= 1 && tl.y0 >= 1 && tl.x0 + SH::TX + 1 <= nx && tl.y0 + SH::TY + 1 <= P.ny;
   unsigned status = 0;
@@ -343,7 +433,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     r2r = fshift<R>(P, 1, ring_t) + d2r;
   }
   // prefetch the next tile's node types
-  if (next_ti < ntiles) tt = load_types<SH>(tiles, insts, next_ti, tid);
+  next_types(tt);
 
   // ---- moments of the own node (Eq. 9), potentials -> shared
   R rho1 = R(0), rho2 = R(0), d1 = R(0), d2 = R(0), j1x = R(0), j1y = R(0), j2x = R(0), j2y = R(0);
@@ -375,11 +465,10 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     }
     R ps = R(0), p1 = R(0), p2 = R(0);
     if (is_live(own_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
-    sp[eo] = ps;
-    sq1[eo] = p1;
-    sq2[eo] = p2;
+    const bool mk = is_live(own_t) && r1 > theta;
+    spot[eo] = Pot<R>{ps, p1, p2, code_bits<R>(node_code(own_t, mk))};
     st_[eo] = own_t;
-    sm_[eo] = (is_live(own_t) && r1 > theta) ? 1 : 0;
+    sm_[eo] = mk ? 1 : 0;
   }
   if (tid < SH::RING) {
     R r1 = r1r, r2 = r2r;
@@ -392,11 +481,10 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     }
     R ps = R(0), p1 = R(0), p2 = R(0);
     if (is_live(ring_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
-    sp[er] = ps;
-    sq1[er] = p1;
-    sq2[er] = p2;
+    const bool mk = is_live(ring_t) && r1 > theta;
+    spot[er] = Pot<R>{ps, p1, p2, code_bits<R>(node_code(ring_t, mk))};
     st_[er] = ring_t;
-    sm_[er] = (is_live(ring_t) && r1 > theta) ? 1 : 0;
+    sm_[er] = mk ? 1 : 0;
   }
   if (__syncthreads_or(waited_ok ? 0 : 1)) return true;
   after_sync();
@@ -408,16 +496,21 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     // stencils sum w (value(x + e) - value(x)) e, equal to the sums of Eqs. 11
     // and 14 since sum_a w e = 0, but free of the cancellation between nearly
     // equal neighbour values in a bulk phase; a solid neighbour contributes 0.
-    const R psc = sp[eo], p1c = sq1[eo], p2c = sq2[eo];
+    const Pot<R> pc = spot[eo];
+    const R psc = pc.ps, p1c = pc.p1, p2c = pc.p2;
+    int cd[9];                       // neighbour codes, reused by the pushes
+    cd[0] = code_of<R>(pc.code);
     R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
       const int en = eo + EY(a) * SH::EXT_X + EX(a);
-      const bool lv = is_live(st_[en]);
+      const Pot<R> q = spot[en];
+      cd[a] = code_of<R>(q.code);
+      const bool lv = (cd[a] & C_LIVE) != 0;
       const R w = wf<R>(a);
-      const R dp = lv ? rsub<R>(sp[en], psc) : R(0);
-      const R d2 = lv ? rsub<R>(sq2[en], p2c) : R(0);
-      const R d1 = lv ? rsub<R>(sq1[en], p1c) : R(0);
+      const R dp = lv ? rsub<R>(q.ps, psc) : R(0);
+      const R d2 = lv ? rsub<R>(q.p2, p2c) : R(0);
+      const R d1 = lv ? rsub<R>(q.p1, p1c) : R(0);
       const R vs = lv ? R(0) : w;
       stencil_acc<R>(spx, w, dp, EX(a)); stencil_acc<R>(s2x, w, d2, EX(a));
       stencil_acc<R>(s1x, w, d1, EX(a)); stencil_add<R>(ssx, vs, EX(a));
@@ -443,7 +536,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     const R urx = u_phys<R>(j1x, j2x, F1x, F2x, rrt);
     const R ury = u_phys<R>(j1y, j2y, F1y, F2y, rrt);
 
-    const bool liq = sm_[eo] != 0;
+    const bool liq = (cd[0] & C_MARK) != 0;
     tout[node] = liq ? T_LIQUID : T_GAS;
 
     // neighbour indices for the push (constant offsets away from the edges)
@@ -461,8 +554,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
         bool vnb = false;
 #pragma unroll
         for (int b = 1; b < 5; ++b) {
-          const int en = eo + EY(b) * SH::EXT_X + EX(b);
-          vnb |= (st_[en] == T_LIQUID && sm_[en] == 0);
+          vnb |= (cd[b] & (C_TYPE | C_MARK)) == T_LIQUID;
         }
         if (appear || vnb) {
           R dC[NS], cb[NS];
@@ -500,7 +592,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
         bool surf = false;
         if (P.r1_surf) {
 #pragma unroll
-          for (int b = 1; b < 5; ++b) surf |= st_[eo + EY(b) * SH::EXT_X + EX(b)] == T_SOLID_D;
+          for (int b = 1; b < 5; ++b) surf |= (cd[b] & C_TYPE) == T_SOLID_D;
         }
         R R1 = rmul<R>(surf ? rp<R>(P).k1_s : rp<R>(P).k1, CA);
         if (P.has_rev)
@@ -540,15 +632,16 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
           st<TF, R>(fo + node, rfma<R>(w, down, fs));
           continue;
         }
-        const int en = eo + EY(a) * SH::EXT_X + EX(a);
-        const uint8_t tn = st_[en];
-        if (is_fluid(tn))
-          st<TF, R>(fo + a * N + nb[a], rfma<R>(w, sm_[en] ? dl : dg, fs));
-        else if (!is_res(tn))
-          st<TF, R>(fo + OPP(a) * N + node, rfma<R>(w, down, fs));
+        // into a fluid neighbour (re-based to its new phase), or bounced back
+        // here from a solid or wall; nothing into a reservoir
+        const int c = cd[a];
+        const bool fl = (c & C_FLUID) != 0;
+        const R sto = fl ? ((c & C_MARK) ? dl : dg) : down;
+        const int off = fl ? a * N + nb[a] : OPP(a) * N + node;
+        if (fl || !(c & C_RES)) st<TF, R>(fo + off, rfma<R>(w, sto, fs));
         // a liquid node flags the minerals on its axis links for the VOP kernel
-        if (s == 0 && a < 5 && liq && is_mineral(tn))
-          atomicOr(&Ip->vmask[nb[a] >> 5], 1u << (nb[a] & 31));
+        if (s == 0 && a < 5 && liq && (c & C_MIN))
+          atomicOr(&V.vmask[nb[a] >> 5], 1u << (nb[a] & 31));
       }
     }
 
@@ -558,19 +651,18 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
           const R eu = R(EX(a)) * urx + R(EY(a)) * ury;
-          int dst = node, slot = a;            // rest population stays
+          // the rest population stays; a moving one goes into a liquid
+          // neighbour, out into a liquid reservoir, or bounces back here
+          // (no-flux / mineral link)
+          int dst = node, slot = a;
           bool keep = true;
           if (a > 0) {
-            const int en = eo + EY(a) * SH::EXT_X + EX(a);
-            const uint8_t tn = st_[en];
-            const bool mn = sm_[en] != 0;
-            if (is_fluid(tn) && mn) {
-              dst = nb[a];                     // into a liquid neighbour
-            } else if (is_res(tn) && mn) {
-              keep = false;                    // outflow into a liquid reservoir
-            } else {
-              slot = OPP(a);                   // no-flux / mineral: bounce back
-            }
+            const int c = cd[a];
+            const bool into = (c & (C_FLUID | C_MARK)) == (C_FLUID | C_MARK);
+            const bool out = (c & (C_RES | C_MARK)) == (C_RES | C_MARK);
+            dst = into ? nb[a] : node;
+            slot = (into || out) ? a : OPP(a);
+            keep = !out;
           }
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
@@ -597,44 +689,69 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const DevInst* Ip, con
     tout[node] = t;
   }
 
-  // ---- warp max of rho_1 over fluid nodes (next step's threshold) and status
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mymax = rmax<R>(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
-  status = __reduce_or_sync(0xffffffffu, status);
-  if (lane == 0) {
-    if (mymax > R(-1.0 / 0.0)) {
-      // exact maximum; the atomic only when it can raise the slot
-      const unsigned long long enc = ord_enc(double(mymax));
-      unsigned long long* slot = &Ip->scal[S_MAX0 + (cur ^ 1)];
-      if (enc > *(volatile unsigned long long*)slot) atomicMax(slot, enc);
-    }
-    if (status) atomicOr(&Ip->scal[S_STATUS], (unsigned long long)status);
-  }
+  // ---- max of rho_1 over fluid nodes (next step's threshold) and status
+  acc.mx = rmax<R>(acc.mx, mymax);
+  acc.status |= status;
   return false;
 }
 
 // Plain bulk kernel: persistent over the tile list, populations loaded from
 // global memory by each thread.  The shared stage is double-buffered, so a
 // tile costs one block barrier.
-template <class SH, class TF, class TG, class R, int NS>
+//
+// SINGLE: every tile belongs to the one simulation at insts[0]; its step view
+// is read once, the next tile's descriptor is loaded a tile ahead, and the
+// maximum and status are flushed once at the end.  Otherwise each tile's
+// instance supplies its own view and the accumulators are flushed per tile.
+template <class SH, class TF, class TG, class R, int NS, bool SINGLE>
 __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const Tile* __restrict__ tiles, int ntiles,
                                                                          const DevInst* __restrict__ insts) {
-  __shared__ R s_psi[2][SH::EXT], s_phi1[2][SH::EXT], s_phi2[2][SH::EXT];
+  __shared__ Pot<R> s_pot[2][SH::EXT];
   __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
-  int ti = next_live(tiles, ntiles, insts, blockIdx.x, gridDim.x);
+  const int stride = gridDim.x;
+  TileAcc<R> acc{R(-1.0 / 0.0), 0u};
   int buf = 0;
   TileTypes tt;
-  if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, threadIdx.x);
-  while (ti < ntiles) {
-    const int nt = next_live(tiles, ntiles, insts, ti + gridDim.x, gridDim.x);
-    const Tile tl = tiles[ti];
-    const DevInst* Ip = insts + tl.inst;
-    const int cur = int(Ip->scal[S_STEP] & 1ULL);
-    const GlobalSrc<TF, TG, R, NS> src{(const TF*)Ip->f[cur], (const TG*)Ip->g[cur], (int)Ip->N};
-    bulk_tile<SH, TF, TG, R, NS>(tl, Ip, Ip->P, src, [] {}, true, tt, tiles, ntiles, insts, nt, s_psi[buf], s_phi1[buf],
-                                 s_phi2[buf], s_t[buf], s_m[buf]);
-    buf ^= 1;
-    ti = nt;
+  if constexpr (SINGLE) {
+    // one simulation: all tiles are live or none is
+    if (!(insts->scal[S_STEP] < insts->scal[S_LIMIT])) return;
+    const StepView<TF, TG, R> V = step_view<TF, TG, R>(insts);
+    const DevParams& P = insts->P;
+    const GlobalSrc<TF, TG, R, NS> src{V.fin, V.gin, V.N};
+    int ti = blockIdx.x;
+    Tile tl = ti < ntiles ? tiles[ti] : Tile{};
+    if (ti < ntiles) tt = load_types<SH>(tl, P, V.tin, threadIdx.x);
+    while (ti < ntiles) {
+      const int nt = ti + stride;
+      const Tile tn = nt < ntiles ? tiles[nt] : Tile{};
+      auto next_types = [&](TileTypes& t) {
+        if (nt < ntiles) t = load_types<SH>(tn, P, V.tin, threadIdx.x);
+      };
+      bulk_tile<SH, TF, TG, R, NS>(tl, V, P, src, [] {}, next_types, true, tt, acc, s_pot[buf], s_t[buf],
+                                   s_m[buf]);
+      buf ^= 1;
+      ti = nt;
+      tl = tn;
+    }
+    flush_acc(acc, V.scal, V.cur);
+  } else {
+    int ti = next_live(tiles, ntiles, insts, blockIdx.x, stride);
+    if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, threadIdx.x);
+    while (ti < ntiles) {
+      const int nt = next_live(tiles, ntiles, insts, ti + stride, stride);
+      const Tile tl = tiles[ti];
+      const DevInst* Ip = insts + tl.inst;
+      const StepView<TF, TG, R> V = step_view<TF, TG, R>(Ip);
+      const GlobalSrc<TF, TG, R, NS> src{V.fin, V.gin, V.N};
+      auto next_types = [&](TileTypes& t) {
+        if (nt < ntiles) t = load_types<SH>(tiles, insts, nt, threadIdx.x);
+      };
+      bulk_tile<SH, TF, TG, R, NS>(tl, V, Ip->P, src, [] {}, next_types, true, tt, acc, s_pot[buf], s_t[buf],
+                                   s_m[buf]);
+      flush_acc(acc, V.scal, V.cur);
+      buf ^= 1;
+      ti = nt;
+    }
   }
 }
 
@@ -709,21 +826,15 @@ struct StageSrc {
   }
 };
 
-// Issue the TMA copies of tile `ti` into a stage (one thread).
-template <class SH, class TG, int NS, int SHAPE>
-__device__ __forceinline__ void stage_issue(const Tile* tiles, const DevInst* insts, int ti, unsigned char* stage,
-                                            uint64_t* bar) {
+// Issue the TMA copies of the tile `d` into a stage (one thread), from the
+// population maps of its step.
+template <class SH, class TG, int NS>
+__device__ __forceinline__ void stage_issue(const Tile& d, const CUtensorMap* mf, const CUtensorMap* mg,
+                                            unsigned char* stage, uint64_t* bar) {
   using C = StageCfg<SH, TG, NS>;
-  const Tile tl = tiles[ti];
-  const DevInst* Ip = insts + tl.inst;
-  const int cur = int(Ip->scal[S_STEP] & 1ULL);
-  const CUtensorMap* mf = &Ip->tmf[SHAPE][cur];
-  const CUtensorMap* mg = &Ip->tmg[SHAPE][cur];
-  tensormap_acquire(mf);
-  if constexpr (NS > 0) tensormap_acquire(mg);
   mbar_arrive_expect_tx(bar, C::TX_BYTES);
-  tma_load_3d(stage + C::FOFF, mf, bar, tl.x0 - STAGE_HALO_X, tl.y0 - 1, 0);
-  if constexpr (NS > 0) tma_load_3d(stage + C::GOFF, mg, bar, tl.x0, tl.y0, 0);
+  tma_load_3d(stage + C::FOFF, mf, bar, d.x0 - STAGE_HALO_X, d.y0 - 1, 0);
+  if constexpr (NS > 0) tma_load_3d(stage + C::GOFF, mg, bar, d.x0, d.y0, 0);
 }
 
 // Staged bulk kernel (FP32 populations): the TMA unit brings each tile's
@@ -736,72 +847,113 @@ __device__ __forceinline__ void stage_issue(const Tile* tiles, const DevInst* in
 // three blocks per SM).  The arithmetic is the plain kernel's, value for
 // value.
 //
-// SINGLE: every tile belongs to one simulation, whose parameter block comes
-// as a kernel argument (read from the constant bank, uniform across the
-// grid); otherwise each tile's instance supplies its own block.
+// SINGLE: every tile belongs to the one simulation at insts[0], whose
+// parameter block comes as a kernel argument (read from the constant bank,
+// uniform across the grid); its step view and population maps are read once,
+// tile descriptors are loaded a tile ahead, and the maximum and status are
+// flushed once at the end.  Otherwise each tile's instance supplies its own
+// block, view and maps, and the accumulators are flushed per tile.
 template <class SH, int SHAPE, class TG, int NS, int STAGES, bool SINGLE>
 __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     k_bulk_tma(const Tile* __restrict__ tiles, int ntiles, const DevInst* __restrict__ insts,
                const __grid_constant__ DevParams Pk) {
   using C = StageCfg<SH, TG, NS>;
   using R = float;
+  using View = StepView<float, TG, R>;
   extern __shared__ __align__(128) unsigned char dyn[];
-  __shared__ R s_psi[2][SH::EXT], s_phi1[2][SH::EXT], s_phi2[2][SH::EXT];
+  __shared__ Pot<R> s_pot[2][SH::EXT];
   __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
   __shared__ __align__(8) uint64_t bars[2];
 
   const int stride = gridDim.x;
-  int ti = next_live(tiles, ntiles, insts, blockIdx.x, stride);
-  int t1 = ti < ntiles ? next_live(tiles, ntiles, insts, ti + stride, stride) : ntiles;
+  View V1{};
+  if constexpr (SINGLE) {
+    // one simulation: all tiles are live or none is
+    if (!(insts->scal[S_STEP] < insts->scal[S_LIMIT])) return;
+    V1 = step_view<float, TG, R>(insts);
+  }
+  auto live = [&](int t) { return SINGLE ? (t < ntiles ? t : ntiles) : next_live(tiles, ntiles, insts, t, stride); };
+  // copies of a tile into a stage (thread 0)
+  auto issue = [&](const Tile& d, unsigned char* stage, uint64_t* bar) {
+    const DevInst* Ip = insts + (SINGLE ? 0 : d.inst);
+    const int cur = SINGLE ? V1.cur : int(Ip->scal[S_STEP] & 1ULL);
+    const CUtensorMap* mf = &Ip->tmf[SHAPE][cur];
+    const CUtensorMap* mg = &Ip->tmg[SHAPE][cur];
+    if constexpr (!SINGLE) {
+      tensormap_acquire(mf);
+      if constexpr (NS > 0) tensormap_acquire(mg);
+    }
+    stage_issue<SH, TG, NS>(d, mf, mg, stage, bar);
+  };
+  int ti = live(blockIdx.x);
+  int t1 = ti < ntiles ? live(ti + stride) : ntiles;
+  Tile d0 = ti < ntiles ? tiles[ti] : Tile{};
+  Tile d1 = t1 < ntiles ? tiles[t1] : Tile{};
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_barrier_init();
+    if constexpr (SINGLE) {
+      tensormap_acquire(&insts->tmf[SHAPE][V1.cur]);
+      if constexpr (NS > 0) tensormap_acquire(&insts->tmg[SHAPE][V1.cur]);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (ti < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, ti, dyn, &bars[0]);
-    if (STAGES == 2 && t1 < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, t1, dyn + C::STAGE, &bars[1]);
+    if (ti < ntiles) issue(d0, dyn, &bars[0]);
+    if (STAGES == 2 && t1 < ntiles) issue(d1, dyn + C::STAGE, &bars[1]);
   }
   TileTypes tt;
-  if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, threadIdx.x);
+  if (ti < ntiles)
+    tt = SINGLE ? load_types<SH>(d0, Pk, V1.tin, threadIdx.x) : load_types<SH>(tiles, insts, ti, threadIdx.x);
+  TileAcc<R> acc{R(-1.0 / 0.0), 0u};
   int j = 0;                        // tiles processed by this block
   uint32_t phase = 0;               // parity bit per stage
   while (ti < ntiles) {
     const int b = STAGES == 2 ? (j & 1) : 0;     // stage of this tile
     const int sb = j & 1;                         // shared buffers of this tile
-    const int t2 = t1 < ntiles ? next_live(tiles, ntiles, insts, t1 + stride, stride) : ntiles;
+    const int t2 = t1 < ntiles ? live(t1 + stride) : ntiles;
+    const Tile d2 = t2 < ntiles ? tiles[t2] : Tile{};
     const bool ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
     phase ^= 1u << b;
-    const Tile tl = tiles[ti];
-    const DevInst* Ip = insts + tl.inst;
-    const int cur = int(Ip->scal[S_STEP] & 1ULL);
+    const DevInst* Ip = insts + (SINGLE ? 0 : d0.inst);
+    const View V = SINGLE ? V1 : step_view<float, TG, R>(Ip);
     unsigned char* stage = dyn + b * C::STAGE;
     const DevParams& P = SINGLE ? Pk : Ip->P;
-    const StageSrc<SH, TG, NS> src{(const float*)(stage + C::FOFF), (const TG*)(stage + C::GOFF),
-                                   (const float*)Ip->f[cur], (int)Ip->N, P.nx, P.ny, tl.x0, tl.y0};
+    const StageSrc<SH, TG, NS> src{(const float*)(stage + C::FOFF), (const TG*)(stage + C::GOFF), V.fin, V.N, P.nx,
+                                   P.ny, d0.x0, d0.y0};
     // after the tile's barrier its stage is free: refill it with the next
     // tile this stage serves
     const int tn = STAGES == 2 ? t2 : t1;
+    const Tile dn = STAGES == 2 ? d2 : d1;
     auto refill = [&] {
-      if (threadIdx.x == 0 && tn < ntiles) stage_issue<SH, TG, NS, SHAPE>(tiles, insts, tn, stage, &bars[b]);
+      if (threadIdx.x == 0 && tn < ntiles) issue(dn, stage, &bars[b]);
     };
-    if (bulk_tile<SH, float, TG, R, NS>(tl, Ip, P, src, refill, ok, tt, tiles, ntiles, insts, t1, s_psi[sb], s_phi1[sb],
-                                        s_phi2[sb], s_t[sb], s_m[sb])) {
+    auto next_types = [&](TileTypes& t) {
+      if (t1 < ntiles)
+        t = SINGLE ? load_types<SH>(d1, Pk, V1.tin, threadIdx.x) : load_types<SH>(tiles, insts, t1, threadIdx.x);
+    };
+    if (bulk_tile<SH, float, TG, R, NS>(d0, V, P, src, refill, next_types, ok, tt, acc, s_pot[sb], s_t[sb],
+                                        s_m[sb])) {
       // a wait gave up: record it, let the copies still in flight land
       // (bounded waits: this tile's stage, and with two stages the next
       // tile's), and leave
+      flush_acc(acc, V.scal, V.cur);
       if (threadIdx.x == 0) {
-        atomicOr(&Ip->scal[S_STATUS], (unsigned long long)ST_TIMEOUT);
+        atomicOr(&V.scal[S_STATUS], (unsigned long long)ST_TIMEOUT);
         mbar_wait_bounded(&bars[b], ((phase >> b) & 1u) ^ 1u);
         if (STAGES == 2 && t1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
       }
       return;
     }
+    if constexpr (!SINGLE) flush_acc(acc, V.scal, V.cur);
     ++j;
     ti = t1;
     t1 = t2;
+    d0 = d1;
+    d1 = d2;
   }
+  if constexpr (SINGLE) flush_acc(acc, V1.scal, V1.cur);
 }
 
 }  // namespace pslbm

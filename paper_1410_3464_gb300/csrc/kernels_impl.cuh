@@ -11,22 +11,26 @@ namespace {
 
 // Persistent grid: as many blocks as fit on the device at once (capped by the
 // tile count); each block walks the tile list with a stride of the grid size.
-template <class SH, int NS>
+template <class SH, int NS, bool SINGLE>
 int bulk_grid(int ntiles) {
   static int cap = 0;
   if (cap == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk<SH, KTF, KTG, KR, NS>, NTHREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bulk<SH, KTF, KTG, KR, NS, SINGLE>, NTHREADS, 0);
     cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
   return ntiles < cap ? ntiles : cap;
 }
+// single: the tile list covers one simulation (insts[0]) only.
 template <class SH, int NS>
-void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts) {
+void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts, bool single) {
   if (ntiles <= 0) return;
-  k_bulk<SH, KTF, KTG, KR, NS><<<bulk_grid<SH, NS>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
+  if (single)
+    k_bulk<SH, KTF, KTG, KR, NS, true><<<bulk_grid<SH, NS, true>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
+  else
+    k_bulk<SH, KTF, KTG, KR, NS, false><<<bulk_grid<SH, NS, false>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
 }
 // Staged variants: grid of as many blocks as fit (two per SM with the
 // double-buffered stage, three with the single stage), dynamic shared memory

@@ -6,7 +6,7 @@
 namespace pslbm {
 
 struct Launchers {
-  void (*bulk[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*);
+  void (*bulk[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*, bool single);
   // TMA-staged bulk kernel (FP32 populations only; null for FP64); single is
   // the host parameter block when the tile list holds one simulation, else null
   void (*bulk_tma[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*, const DevParams* single);

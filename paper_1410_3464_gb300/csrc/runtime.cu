@@ -363,7 +363,7 @@ void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int staged, int
     else if (staged == 1)
       st.L->bulk_tma[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
     else
-      st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d);
+      st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single != nullptr);
     st.L->vop(s, st.ninst, st.d, st.max_words);
     st.L->amend(s, st.ninst, st.d);
   }
@@ -808,7 +808,7 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
     else if (h->run.staged == 1)
       h->L->bulk_tma[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, &h->h.P);
     else
-      h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d);
+      h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, true);
     cudaEventRecord(ev[1], s);
     h->L->vop(s, 1, h->d, h->run.max_words);
     cudaEventRecord(ev[2], s);
