@@ -632,8 +632,10 @@ class Lattice:
                     Jw = (1.0 - p["J0"][iB]) / 4.0
                     kap = k2 / (2.0 * Jw)
                     out = gstar[iB, d]
-                    back = (out * (1.0 - kap)) / (1.0 + kap)
-                    q = out - back
+                    # back = out (1 - kap) / (1 + kap); the flux out - back
+                    # written without the cancellation of two near values
+                    q = out * (2.0 * kap / (1.0 + kap))
+                    back = out - q
                     gnew[iB, a] = np.where(onD, back, gnew[iB, a])
                     qB[d] = np.where(onD, q, 0.0)
                     if iE >= 0:
@@ -642,9 +644,11 @@ class Lattice:
                     Jw = (1.0 - p["J0"][iF]) / 4.0
                     kap = k4 / (2.0 * Jw)
                     out = gstar[iF, d]
-                    back = (out * (1.0 - kap) + k4 * Csat) / (1.0 + kap)
+                    # back = (out (1 - kap) + k4 C_sat) / (1 + kap), flux as above
+                    q = out * (2.0 * kap / (1.0 + kap)) - k4 * Csat / (1.0 + kap)
+                    back = out - q
                     gnew[iF, a] = np.where(onM, back, gnew[iF, a])
-                    qF[d] = np.where(onM, out - back, 0.0)
+                    qF[d] = np.where(onM, q, 0.0)
 
         # 7. VOP volume update (Eqs. 33, 35) and status decisions
         V = self.V.copy()

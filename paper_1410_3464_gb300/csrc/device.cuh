@@ -72,6 +72,9 @@ struct DevParamsR {
   R J0[MAXS], Ja[MAXS], inv_tau_g[MAXS], shift_c[MAXS], conc_in[MAXS], cR1[MAXS], cR3[MAXS];
   R k1, k1_inv_Keq, k3, k2, k4, C_F_sat, gas_yield, inv_M_C, c_total_per_rho1;
   R k1_s, k1_inv_Keq_s;   // R1 constants at liquid nodes touching D(s) (surface factor applied)
+  // reactive link rule (Eqs. 29-31 as a halfway wall): link flux q = out * qa - qc,
+  // returning population out - q, out = stored + sh (the stored shift J_a C_0 undone)
+  R vB_qa, vB_sh, vF_qa, vF_qc, vF_sh;
 };
 
 struct DevParams {

@@ -17,7 +17,9 @@ namespace pslbm {
 // the outgoing population `out`, J_w = (1 - J0)/4 and kappa = k / (2 J_w),
 // the returning population is (out (1 - kappa) + k C_sat) / (1 + kappa) and the
 // link flux q = out - back is the amount consumed (B by R2 at D(s), F by R4 at
-// D(s) or F(s)); E gains the B consumed on the same link.  Then V_D -= Vbar_D
+// D(s) or F(s)); E gains the B consumed on the same link.  The flux is computed
+// directly, q = out 2 kappa / (1 + kappa) - k C_sat / (1 + kappa), since out and
+// back differ by a relative 2 kappa only.  Then V_D -= Vbar_D
 // sum q_B, V_F += Vbar_F sum q_F, and the node dissolves, overflows or changes
 // between D(s) and F(s).
 //
@@ -77,23 +79,21 @@ __device__ __forceinline__ void vop_node(const DevInst* Ip, const DevParams& P, 
       if (nn < 0) continue;
       if (useB) {
         const int iB = P.iB;
-        const R Ja = rp<R>(P).Ja[iB], sh = Ja * rp<R>(P).shift_c[iB];
+        const R sh = rp<R>(P).vB_sh;
         const R out = oB[b - 1] + sh;
-        const R kap = rp<R>(P).k2 / (R(2) * Ja);
-        const R bk = out * (R(1) - kap) / (R(1) + kap);
-        const R q = out - bk;
+        const R q = out * rp<R>(P).vB_qa;
+        const R bk = out - q;
         st<TG, R>(gout + (iB * 5 + b) * N + nn, bk - sh);
         sB += q;
         if (P.iE >= 0) st<TG, R>(gout + (P.iE * 5 + b) * N + nn, oE[b - 1] + q);
       }
       if (useF) {
         const int iF = P.iF;
-        const R Ja = rp<R>(P).Ja[iF], sh = Ja * rp<R>(P).shift_c[iF];
+        const R sh = rp<R>(P).vF_sh;
         const R out = oF[b - 1] + sh;
-        const R kap = rp<R>(P).k4 / (R(2) * Ja);
-        const R bk = (out * (R(1) - kap) + rp<R>(P).k4 * rp<R>(P).C_F_sat) / (R(1) + kap);
-        st<TG, R>(gout + (iF * 5 + b) * N + nn, bk - sh);
-        sF += out - bk;
+        const R q = out * rp<R>(P).vF_qa - rp<R>(P).vF_qc;
+        st<TG, R>(gout + (iF * 5 + b) * N + nn, (out - q) - sh);
+        sF += q;
       }
     }
   }

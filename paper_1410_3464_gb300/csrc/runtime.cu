@@ -225,6 +225,20 @@ void fill_r(DevParamsR<R>& q, const DevParams& P) {
   q.gas_yield = R(P.gas_yield);
   q.inv_M_C = R(P.inv_M_C);
   q.c_total_per_rho1 = R(P.c_total_per_rho1);
+  // link rule with kappa = k / (2 J_w), J_w = J_a: back = (out (1 - kappa) + k C_sat) / (1 + kappa),
+  // flux q = out - back = out 2 kappa / (1 + kappa) - k C_sat / (1 + kappa) (no cancellation)
+  q.vB_qa = q.vB_sh = q.vF_qa = q.vF_qc = q.vF_sh = R(0);
+  if (P.iB >= 0) {
+    const double kap = P.k2 / (2.0 * P.Ja[P.iB]);
+    q.vB_qa = R(2.0 * kap / (1.0 + kap));
+    q.vB_sh = R(P.Ja[P.iB] * P.shift_c[P.iB]);
+  }
+  if (P.iF >= 0) {
+    const double kap = P.k4 / (2.0 * P.Ja[P.iF]);
+    q.vF_qa = R(2.0 * kap / (1.0 + kap));
+    q.vF_qc = R(P.k4 * P.C_F_sat / (1.0 + kap));
+    q.vF_sh = R(P.Ja[P.iF] * P.shift_c[P.iF]);
+  }
 }
 
 DevParams to_dev(const pslbm_params* p) {
