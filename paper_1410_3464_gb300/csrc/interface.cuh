@@ -24,9 +24,10 @@ namespace pslbm {
 // between D(s) and F(s).
 //
 // The bulk kernel sets a bit for every mineral node a liquid node touched in
-// the step (the only nodes this kernel changes); each warp takes one 32-bit
-// word of that bitmap, lane i handles node 32 w + i when its bit is set, and
-// lane 0 clears the word.
+// the step (the only nodes this kernel changes).  Each warp takes a chunk of
+// VOP_CHUNK consecutive words of that bitmap, clears them, and deals the set
+// bits of the chunk out to its lanes in node order (32 nodes per round), so
+// that every lane of a round has a node to update.
 template <class TF, class TG, class R, int NS>
 __device__ __forceinline__ void vop_node(const DevInst* Ip, const DevParams& P, int N, int cur,
                                          unsigned long long step, int node) {
@@ -130,24 +131,64 @@ __device__ __forceinline__ void vop_node(const DevInst* Ip, const DevParams& P, 
   }
 }
 
+// Blocks per SM the VOP kernel's register budget targets (its grid is one
+// wave of resident blocks): five in FP32, four in FP64 (twice the registers
+// per value).
+template <class R>
+constexpr int vop_min_blocks() {
+  return sizeof(R) == 8 ? 4 : 5;
+}
+
+// Bitmap words per warp chunk of the VOP kernel.
+constexpr int VOP_CHUNK = 8;
+
 template <class TF, class TG, class R, int NS>
-__global__ void __launch_bounds__(NTHREADS) k_vop(const DevInst* __restrict__ insts, int ninst) {
+__global__ void __launch_bounds__(NTHREADS, vop_min_blocks<R>()) k_vop(const DevInst* __restrict__ insts, int ninst) {
+  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int ws = (gridDim.x * blockDim.x) >> 5;
+  const int c0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int cs = (gridDim.x * blockDim.x) >> 5;
   for (int ii = 0; ii < ninst; ++ii) {
     const DevInst* Ip = insts + ii;
     const unsigned long long step = Ip->scal[S_STEP];
     if (step >= Ip->scal[S_LIMIT]) continue;   // frozen instance
     const int N = (int)Ip->N;
     const int nw = (N + 31) >> 5;
+    const int nchunk = (nw + VOP_CHUNK - 1) / VOP_CHUNK;
     const int cur = int(step & 1ULL);
-    for (int w = w0; w < nw; w += ws) {
-      const unsigned m = Ip->vmask[w];        // the same word for the whole warp
-      if (m == 0u) continue;
-      __syncwarp();
-      if (lane == 0) Ip->vmask[w] = 0u;
-      if (m & (1u << lane)) vop_node<TF, TG, R, NS>(Ip, Ip->P, N, cur, step, (w << 5) + lane);
+    unsigned* vmask = Ip->vmask;
+    for (int c = c0; c < nchunk; c += cs) {
+      // lane j < VOP_CHUNK holds word c VOP_CHUNK + j, and the number of set
+      // bits before it in the chunk
+      const int wj = c * VOP_CHUNK + lane;
+      const unsigned m = (lane < VOP_CHUNK && wj < nw) ? vmask[wj] : 0u;
+      if (m) vmask[wj] = 0u;
+      const int cnt = __popc(m);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < VOP_CHUNK; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int total = __shfl_sync(FULL, incl, VOP_CHUNK - 1);
+      const int excl = incl - cnt;
+      for (int r = 0; r < total; r += 32) {
+        // the k-th set bit of the chunk: its word j and its rank within it
+        const int k = r + lane;
+        int node = -1;
+#pragma unroll
+        for (int j = 0; j < VOP_CHUNK; ++j) {
+          const int ej = __shfl_sync(FULL, excl, j);
+          const int nj = __shfl_sync(FULL, cnt, j);
+          const unsigned mj = __shfl_sync(FULL, m, j);
+          if (k >= ej && k < ej + nj) {
+            unsigned mm = mj;
+            for (int i = k - ej; i > 0; --i) mm &= mm - 1u;   // drop the lower set bits
+            node = (c * VOP_CHUNK + j) * 32 + (__ffs(mm) - 1);
+          }
+        }
+        if (node >= 0) vop_node<TF, TG, R, NS>(Ip, Ip->P, N, cur, step, node);
+      }
     }
   }
 }

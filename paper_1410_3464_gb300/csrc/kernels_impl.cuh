@@ -69,19 +69,22 @@ void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* in
         <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, unused);
   }
 }
-// Grid over the interface bitmap words of the largest member (one word per
-// warp), capped at 8 resident blocks per SM (warps then stride).
+// Grid over the interface bitmap of the largest member (one chunk of
+// VOP_CHUNK words per warp), capped at one wave of resident blocks (warps
+// then stride).
 template <int NS>
 void vop_l(cudaStream_t s, int ninst, const DevInst* insts, long long max_words) {
   if (ninst <= 0 || max_words <= 0) return;
   static int cap = 0;
   if (cap == 0) {
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cap = (sms > 0 ? sms : 1) * 8;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vop<KTF, KTG, KR, NS>, NTHREADS, 0);
+    cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
-  const long long need = (max_words * 32 + NTHREADS - 1) / NTHREADS;
+  const long long chunks = (max_words + VOP_CHUNK - 1) / VOP_CHUNK;
+  const long long need = (chunks * 32 + NTHREADS - 1) / NTHREADS;
   k_vop<KTF, KTG, KR, NS><<<int(need < cap ? need : cap), NTHREADS, 0, s>>>(insts, ninst);
 }
 template <int NS>
