@@ -140,7 +140,7 @@ constexpr int vop_min_blocks() {
 }
 
 // Bitmap words per warp chunk of the VOP kernel.
-constexpr int VOP_CHUNK = 8;
+constexpr int VOP_CHUNK = 4;
 
 template <class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS, vop_min_blocks<R>()) k_vop(const DevInst* __restrict__ insts, int ninst) {
@@ -199,9 +199,10 @@ __device__ __forceinline__ bool surv_liquid(uint8_t tf) { return tf == T_LIQUID;
 // End of a step for one instance: decode the next step's liquid threshold
 // (half the maximum the bulk kernel gathered this step) into both precisions,
 // free the slot this step read (it receives the maximum two steps later) and
-// advance the step counter.
-__device__ __forceinline__ void finish_step(const DevInst* Ip, unsigned long long step) {
-  const double th = 0.5 * ord_dec(Ip->scal[S_MAX0 + int((step + 1) & 1ULL)]);
+// advance the step counter.  mx: the encoded maximum of this step's slot,
+// S_MAX0 + ((step + 1) & 1).
+__device__ __forceinline__ void finish_step(const DevInst* Ip, unsigned long long step, unsigned long long mx) {
+  const double th = 0.5 * ord_dec(mx);
   Ip->scal[S_THETA] = (unsigned long long)__double_as_longlong(th);
   Ip->scal[S_THETAF] = (unsigned long long)(unsigned)__float_as_int(float(th));
   Ip->scal[S_MAX0 + int(step & 1ULL)] = 0ULL;
@@ -212,11 +213,14 @@ __device__ __forceinline__ void finish_step(const DevInst* Ip, unsigned long lon
 template <class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ insts) {
   const DevInst* Ip = insts + blockIdx.x;
-  const unsigned long long step = Ip->scal[S_STEP];
-  if (step >= Ip->scal[S_LIMIT]) return;   // frozen instance
-  const unsigned long long nev_raw = Ip->scal[S_NEVENT];
+  // the counters this kernel reads, loaded together (one memory round trip)
+  const volatile unsigned long long* sc = Ip->scal;
+  const unsigned long long step = sc[S_STEP], limit = sc[S_LIMIT], nev_raw = sc[S_NEVENT], m0 = sc[S_MAX0],
+                           m1 = sc[S_MAX1];
+  if (step >= limit) return;   // frozen instance
+  const unsigned long long mx = (step & 1ULL) ? m0 : m1;
   if (nev_raw == 0) {
-    if (threadIdx.x == 0) finish_step(Ip, step);
+    if (threadIdx.x == 0) finish_step(Ip, step, mx);
     return;
   }
   const DevParams& P = Ip->P;
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
   for (int i = threadIdx.x; i < nv; i += blockDim.x) Ip->claim[vlist[i]] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < nev; i += blockDim.x) Ip->evt[Ip->evlist[i]] = 0;
-  if (threadIdx.x == 0) finish_step(Ip, step);
+  if (threadIdx.x == 0) finish_step(Ip, step, mx);
 }
 
 }  // namespace pslbm
