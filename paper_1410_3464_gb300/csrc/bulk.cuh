@@ -322,10 +322,13 @@ template <class R>
 struct alignas(4 * sizeof(R)) Pot {
   R ps, p1, p2, code;
 };
-constexpr int C_TYPE = 0x7, C_MARK = 1 << 3, C_FLUID = 1 << 4, C_LIVE = 1 << 5, C_RES = 1 << 6, C_MIN = 1 << 7;
+// Code bits: the low nibble holds what a push needs of a neighbour (fluid,
+// liquid marking, reservoir, mineral), then live, an axis-link pair (raw
+// type liquid, raw type D(s)) and the raw type.
+constexpr int C_FLUID = 1, C_MARK = 2, C_RES = 4, C_MIN = 8, C_LIVE = 16, C_OLDLIQ = 32, C_SOLD = 64;
 __device__ __forceinline__ int node_code(uint8_t t, bool mark) {
-  return int(t) | (mark ? C_MARK : 0) | (is_fluid(t) ? C_FLUID : 0) | (is_live(t) ? C_LIVE : 0) |
-         (is_res(t) ? C_RES : 0) | (is_mineral(t) ? C_MIN : 0);
+  return (is_fluid(t) ? C_FLUID : 0) | (mark ? C_MARK : 0) | (is_res(t) ? C_RES : 0) | (is_mineral(t) ? C_MIN : 0) |
+         (is_live(t) ? C_LIVE : 0) | (t == T_LIQUID ? C_OLDLIQ : 0) | (t == T_SOLID_D ? C_SOLD : 0) | (int(t) << 8);
 }
 template <class R> __device__ __forceinline__ R code_bits(int c);
 template <> __device__ __forceinline__ float code_bits<float>(int c) { return __int_as_float(c); }
@@ -498,15 +501,20 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
     // equal neighbour values in a bulk phase; a solid neighbour contributes 0.
     const Pot<R> pc = spot[eo];
     const R psc = pc.ps, p1c = pc.p1, p2c = pc.p2;
-    int cd[9];                       // neighbour codes, reused by the pushes
-    cd[0] = code_of<R>(pc.code);
+    // neighbour codes kept for the pushes: the low nibble of each of the eight
+    // neighbours (nbits, 4 bits per direction) and the raw-type pair of the four
+    // axis neighbours (abits, 2 bits per direction)
+    unsigned nbits = 0u, abits = 0u;
+    const int c0 = code_of<R>(pc.code);
     R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
       const int en = eo + EY(a) * SH::EXT_X + EX(a);
       const Pot<R> q = spot[en];
-      cd[a] = code_of<R>(q.code);
-      const bool lv = (cd[a] & C_LIVE) != 0;
+      const int ca = code_of<R>(q.code);
+      nbits |= unsigned(ca & 0xF) << (4 * (a - 1));
+      if (a < 5) abits |= unsigned((ca >> 5) & 0x3) << (2 * (a - 1));
+      const bool lv = (ca & C_LIVE) != 0;
       const R w = wf<R>(a);
       const R dp = lv ? rsub<R>(q.ps, psc) : R(0);
       const R d2 = lv ? rsub<R>(q.p2, p2c) : R(0);
@@ -536,7 +544,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
     const R urx = u_phys<R>(j1x, j2x, F1x, F2x, rrt);
     const R ury = u_phys<R>(j1y, j2y, F1y, F2y, rrt);
 
-    const bool liq = (cd[0] & C_MARK) != 0;
+    const bool liq = (c0 & C_MARK) != 0;
     tout[node] = liq ? T_LIQUID : T_GAS;
 
     // neighbour indices for the push (constant offsets away from the edges)
@@ -554,7 +562,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
         bool vnb = false;
 #pragma unroll
         for (int b = 1; b < 5; ++b) {
-          vnb |= (cd[b] & (C_TYPE | C_MARK)) == T_LIQUID;
+          // a neighbour that was liquid and is no longer marked liquid
+          vnb |= ((abits >> (2 * (b - 1))) & 1u) && !((nbits >> (4 * (b - 1))) & C_MARK);
         }
         if (appear || vnb) {
           R dC[NS], cb[NS];
@@ -592,7 +601,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
         bool surf = false;
         if (P.r1_surf) {
 #pragma unroll
-          for (int b = 1; b < 5; ++b) surf |= (cd[b] & C_TYPE) == T_SOLID_D;
+          for (int b = 1; b < 5; ++b) surf |= ((abits >> (2 * (b - 1) + 1)) & 1u) != 0;
         }
         R R1 = rmul<R>(surf ? rp<R>(P).k1_s : rp<R>(P).k1, CA);
         if (P.has_rev)
@@ -634,7 +643,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
         }
         // into a fluid neighbour (re-based to its new phase), or bounced back
         // here from a solid or wall; nothing into a reservoir
-        const int c = cd[a];
+        const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
         const bool fl = (c & C_FLUID) != 0;
         const R sto = fl ? ((c & C_MARK) ? dl : dg) : down;
         const int off = fl ? a * N + nb[a] : OPP(a) * N + node;
@@ -657,7 +666,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
           int dst = node, slot = a;
           bool keep = true;
           if (a > 0) {
-            const int c = cd[a];
+            const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
             const bool into = (c & (C_FLUID | C_MARK)) == (C_FLUID | C_MARK);
             const bool out = (c & (C_RES | C_MARK)) == (C_RES | C_MARK);
             dst = into ? nb[a] : node;
@@ -887,8 +896,10 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
   };
   int ti = live(blockIdx.x);
   int t1 = ti < ntiles ? live(ti + stride) : ntiles;
+  // one simulation: tile descriptors ride a tile ahead in registers; a batch
+  // loads them where they are used (fewer live registers on its longer path)
   Tile d0 = ti < ntiles ? tiles[ti] : Tile{};
-  Tile d1 = t1 < ntiles ? tiles[t1] : Tile{};
+  Tile d1 = SINGLE && t1 < ntiles ? tiles[t1] : Tile{};
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -901,7 +912,7 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
   __syncthreads();
   if (threadIdx.x == 0) {
     if (ti < ntiles) issue(d0, dyn, &bars[0]);
-    if (STAGES == 2 && t1 < ntiles) issue(d1, dyn + C::STAGE, &bars[1]);
+    if (STAGES == 2 && t1 < ntiles) issue(SINGLE ? d1 : tiles[t1], dyn + C::STAGE, &bars[1]);
   }
   TileTypes tt;
   if (ti < ntiles)
@@ -913,9 +924,10 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     const int b = STAGES == 2 ? (j & 1) : 0;     // stage of this tile
     const int sb = j & 1;                         // shared buffers of this tile
     const int t2 = t1 < ntiles ? live(t1 + stride) : ntiles;
-    const Tile d2 = t2 < ntiles ? tiles[t2] : Tile{};
+    const Tile d2 = SINGLE && t2 < ntiles ? tiles[t2] : Tile{};
     const bool ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
     phase ^= 1u << b;
+    if constexpr (!SINGLE) d0 = tiles[ti];
     const DevInst* Ip = insts + (SINGLE ? 0 : d0.inst);
     const View V = SINGLE ? V1 : step_view<float, TG, R>(Ip);
     unsigned char* stage = dyn + b * C::STAGE;
@@ -925,9 +937,8 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     // after the tile's barrier its stage is free: refill it with the next
     // tile this stage serves
     const int tn = STAGES == 2 ? t2 : t1;
-    const Tile dn = STAGES == 2 ? d2 : d1;
     auto refill = [&] {
-      if (threadIdx.x == 0 && tn < ntiles) issue(dn, stage, &bars[b]);
+      if (threadIdx.x == 0 && tn < ntiles) issue(SINGLE ? (STAGES == 2 ? d2 : d1) : tiles[tn], stage, &bars[b]);
     };
     auto next_types = [&](TileTypes& t) {
       if (t1 < ntiles)
@@ -950,8 +961,10 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     ++j;
     ti = t1;
     t1 = t2;
-    d0 = d1;
-    d1 = d2;
+    if constexpr (SINGLE) {
+      d0 = d1;
+      d1 = d2;
+    }
   }
   if constexpr (SINGLE) flush_acc(acc, V1.scal, V1.cur);
 }

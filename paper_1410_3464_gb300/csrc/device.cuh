@@ -20,6 +20,8 @@ constexpr uint8_t T_VANISH = 0x80;   // flag: liquid -> solid this step
 // one-node ring.  The runtime picks the faster shape per handle or batch by
 // timing its first steps (results do not depend on the shape).
 constexpr int NTHREADS = 256;
+// Interface-bitmap words per warp chunk of the VOP kernel.
+constexpr int VOP_CHUNK = 4;
 template <int TX_, int TY_>
 struct TileShape {
   static constexpr int TX = TX_, TY = TY_;

@@ -139,56 +139,57 @@ constexpr int vop_min_blocks() {
   return sizeof(R) == 8 ? 4 : 5;
 }
 
-// Bitmap words per warp chunk of the VOP kernel.
-constexpr int VOP_CHUNK = 4;
-
+// chunk_map: (instance, chunk within it) of every chunk of a batch, in
+// instance order, or null for one simulation (instance 0, chunk g); nchunks:
+// the number of chunks.  Warps take chunks with a grid stride, so every
+// member's chunks are spread over the whole grid.
 template <class TF, class TG, class R, int NS>
-__global__ void __launch_bounds__(NTHREADS, vop_min_blocks<R>()) k_vop(const DevInst* __restrict__ insts, int ninst) {
+__global__ void __launch_bounds__(NTHREADS, vop_min_blocks<R>())
+    k_vop(const DevInst* __restrict__ insts, const int2* __restrict__ chunk_map, long long nchunks) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int c0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int cs = (gridDim.x * blockDim.x) >> 5;
-  for (int ii = 0; ii < ninst; ++ii) {
-    const DevInst* Ip = insts + ii;
+  const long long c0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long cs = (gridDim.x * (long long)blockDim.x) >> 5;
+  for (long long g = c0; g < nchunks; g += cs) {
+    const int2 ic = chunk_map ? chunk_map[g] : make_int2(0, (int)g);
+    const DevInst* Ip = insts + ic.x;
+    const int c = ic.y;
     const unsigned long long step = Ip->scal[S_STEP];
     if (step >= Ip->scal[S_LIMIT]) continue;   // frozen instance
     const int N = (int)Ip->N;
     const int nw = (N + 31) >> 5;
-    const int nchunk = (nw + VOP_CHUNK - 1) / VOP_CHUNK;
     const int cur = int(step & 1ULL);
     unsigned* vmask = Ip->vmask;
-    for (int c = c0; c < nchunk; c += cs) {
-      // lane j < VOP_CHUNK holds word c VOP_CHUNK + j, and the number of set
-      // bits before it in the chunk
-      const int wj = c * VOP_CHUNK + lane;
-      const unsigned m = (lane < VOP_CHUNK && wj < nw) ? vmask[wj] : 0u;
-      if (m) vmask[wj] = 0u;
-      const int cnt = __popc(m);
-      int incl = cnt;
+    // lane j < VOP_CHUNK holds word c VOP_CHUNK + j, and the number of set
+    // bits before it in the chunk
+    const int wj = c * VOP_CHUNK + lane;
+    const unsigned m = (lane < VOP_CHUNK && wj < nw) ? vmask[wj] : 0u;
+    if (m) vmask[wj] = 0u;
+    const int cnt = __popc(m);
+    int incl = cnt;
 #pragma unroll
-      for (int o = 1; o < VOP_CHUNK; o <<= 1) {
-        const int v = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int total = __shfl_sync(FULL, incl, VOP_CHUNK - 1);
-      const int excl = incl - cnt;
-      for (int r = 0; r < total; r += 32) {
-        // the k-th set bit of the chunk: its word j and its rank within it
-        const int k = r + lane;
-        int node = -1;
+    for (int o = 1; o < VOP_CHUNK; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, VOP_CHUNK - 1);
+    const int excl = incl - cnt;
+    for (int r = 0; r < total; r += 32) {
+      // the k-th set bit of the chunk: its word j and its rank within it
+      const int k = r + lane;
+      int node = -1;
 #pragma unroll
-        for (int j = 0; j < VOP_CHUNK; ++j) {
-          const int ej = __shfl_sync(FULL, excl, j);
-          const int nj = __shfl_sync(FULL, cnt, j);
-          const unsigned mj = __shfl_sync(FULL, m, j);
-          if (k >= ej && k < ej + nj) {
-            unsigned mm = mj;
-            for (int i = k - ej; i > 0; --i) mm &= mm - 1u;   // drop the lower set bits
-            node = (c * VOP_CHUNK + j) * 32 + (__ffs(mm) - 1);
-          }
+      for (int j = 0; j < VOP_CHUNK; ++j) {
+        const int ej = __shfl_sync(FULL, excl, j);
+        const int nj = __shfl_sync(FULL, cnt, j);
+        const unsigned mj = __shfl_sync(FULL, m, j);
+        if (k >= ej && k < ej + nj) {
+          unsigned mm = mj;
+          for (int i = k - ej; i > 0; --i) mm &= mm - 1u;   // drop the lower set bits
+          node = (c * VOP_CHUNK + j) * 32 + (__ffs(mm) - 1);
         }
-        if (node >= 0) vop_node<TF, TG, R, NS>(Ip, Ip->P, N, cur, step, node);
       }
+      if (node >= 0) vop_node<TF, TG, R, NS>(Ip, Ip->P, N, cur, step, node);
     }
   }
 }

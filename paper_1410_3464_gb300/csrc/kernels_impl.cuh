@@ -69,12 +69,12 @@ void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* in
         <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, unused);
   }
 }
-// Grid over the interface bitmap of the largest member (one chunk of
-// VOP_CHUNK words per warp), capped at one wave of resident blocks (warps
-// then stride).
+// Grid over the chunks of VOP_CHUNK interface-bitmap words of all members
+// (one chunk per warp), capped at one wave of resident blocks (warps then
+// stride).
 template <int NS>
-void vop_l(cudaStream_t s, int ninst, const DevInst* insts, long long max_words) {
-  if (ninst <= 0 || max_words <= 0) return;
+void vop_l(cudaStream_t s, const DevInst* insts, const int2* chunk_map, long long nchunks) {
+  if (nchunks <= 0) return;
   static int cap = 0;
   if (cap == 0) {
     int dev = 0, sms = 0, per = 0;
@@ -83,9 +83,8 @@ void vop_l(cudaStream_t s, int ninst, const DevInst* insts, long long max_words)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vop<KTF, KTG, KR, NS>, NTHREADS, 0);
     cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
-  const long long chunks = (max_words + VOP_CHUNK - 1) / VOP_CHUNK;
-  const long long need = (chunks * 32 + NTHREADS - 1) / NTHREADS;
-  k_vop<KTF, KTG, KR, NS><<<int(need < cap ? need : cap), NTHREADS, 0, s>>>(insts, ninst);
+  const long long need = (nchunks * 32 + NTHREADS - 1) / NTHREADS;
+  k_vop<KTF, KTG, KR, NS><<<int(need < cap ? need : cap), NTHREADS, 0, s>>>(insts, chunk_map, nchunks);
 }
 template <int NS>
 void amend_l(cudaStream_t s, int ninst, const DevInst* insts) {

@@ -12,8 +12,9 @@ struct Launchers {
   void (*bulk_tma[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*, const DevParams* single);
   // TMA-staged bulk kernel with a single stage and three blocks per SM
   void (*bulk_tma1[NSHAPES])(cudaStream_t, const Tile*, int ntiles, const DevInst*, const DevParams* single);
-  // max_words: the largest interface-bitmap size of the members, (N + 31) / 32
-  void (*vop)(cudaStream_t, int ninst, const DevInst*, long long max_words);
+  // chunk_map: (member, chunk) of every VOP chunk of a batch (null for one
+  // simulation); nchunks: their number
+  void (*vop)(cudaStream_t, const DevInst*, const int2* chunk_map, long long nchunks);
   void (*amend)(cudaStream_t, int ninst, const DevInst*);
   void (*init)(cudaStream_t, DevInst*, const uint8_t*, const double*, const double*, const double*, long long N);
   void (*fields)(cudaStream_t, const DevInst*, long long N, double*, double*, double*, double*, double*, uint8_t*);

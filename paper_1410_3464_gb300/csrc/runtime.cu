@@ -61,12 +61,15 @@ struct Stepper {
   int fix_staged = -1;
   bool staged_ok = false;                  // every instance has TMA descriptors
   const DevParams* single = nullptr;       // host parameters of a one-simulation stepper
-  long long max_words = 0;                 // largest interface bitmap of the instances
+  int2* chunk_map = nullptr;               // (instance, chunk) of every VOP chunk of a batch (device)
+  long long nchunks = 0;                   // VOP chunks of all instances
   bool tuned = false;                      // variant chosen (by timing or by the caller)
   GraphCache graphs;
   double trial_ms[NSHAPES][NSTAGING] = {};
   void release() {
     graphs.clear();
+    if (chunk_map) cudaFree(chunk_map);
+    chunk_map = nullptr;
     for (int s = 0; s < NSHAPES; ++s) {
       if (tiles[s]) cudaFree(tiles[s]);
       tiles[s] = nullptr;
@@ -378,7 +381,7 @@ void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int staged, int
       st.L->bulk_tma[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
     else
       st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single != nullptr);
-    st.L->vop(s, st.ninst, st.d, st.max_words);
+    st.L->vop(s, st.d, st.chunk_map, st.nchunks);
     st.L->amend(s, st.ninst, st.d);
   }
 }
@@ -763,7 +766,7 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   h->run.d = h->d;
   h->run.ninst = 1;
   h->run.dims.assign(1, {p->nx, p->ny});
-  h->run.max_words = (N + 31) / 32;
+  h->run.nchunks = ((N + 31) / 32 + VOP_CHUNK - 1) / VOP_CHUNK;
   h->run.single = &h->h.P;
   choose(h->run);
   {
@@ -824,7 +827,7 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
     else
       h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, true);
     cudaEventRecord(ev[1], s);
-    h->L->vop(s, 1, h->d, h->run.max_words);
+    h->L->vop(s, h->d, nullptr, h->run.nchunks);
     cudaEventRecord(ev[2], s);
     h->L->amend(s, 1, h->d);
     cudaEventRecord(ev[3], s);
@@ -1062,11 +1065,20 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
     b->members.push_back(members[i]);
     di.push_back(members[i]->h);
     b->run.dims.push_back({members[i]->p.nx, members[i]->p.ny});
-    b->run.max_words = std::max(b->run.max_words, (members[i]->N + 31) / 32);
   }
+  // VOP chunks of all members, in member order
+  std::vector<int2> cmap;
+  for (int i = 0; i < n; ++i) {
+    const long long nc = ((members[i]->N + 31) / 32 + VOP_CHUNK - 1) / VOP_CHUNK;
+    for (long long c = 0; c < nc; ++c) cmap.push_back(make_int2(i, (int)c));
+  }
+  b->run.nchunks = (long long)cmap.size();
   cudaStream_t s = lib_stream();
   cudaError_t e = cudaMalloc(&b->d, di.size() * sizeof(DevInst));
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d, di.data(), di.size() * sizeof(DevInst), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMalloc(&b->run.chunk_map, cmap.size() * sizeof(int2));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->run.chunk_map, cmap.data(), cmap.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   b->L = members[0]->L;
   b->run.L = b->L;
