@@ -320,11 +320,16 @@ class Lattice:
     def _forces(self, typ, rho1, rho2, r1res, r2res):
         """Eqs. 11-16: F_1 = F_11 + F_12 + F_1w + rho_1 g, F_2 = F_21 + F_2w + rho_2 g.
         In the cohesion (Eq. 11) and inter-component (Eq. 14) sums a solid
-        neighbour takes the centre node's own psi / phi (neutral wall), so that
-        with w = 0 the wall is neither wetting nor non-wetting (90 degrees, as
-        App. A2 states); wetting is set only by the adhesion term of Eq. 16,
-        whose wall density s is 1 at solid nodes (and outside a non-periodic
-        edge) and 0 at fluid and reservoir nodes."""
+        neighbour takes the value of its mirror image across the wall (a
+        symmetry wall), so that with w = 0 the wall is neither wetting nor
+        non-wetting (90 degrees, as App. A2 and Section 5 state):
+          * an axis neighbour's mirror image is the centre node itself;
+          * a diagonal neighbour (x + ex, y + ey) on a flat wall is mirrored
+            onto the live one of (x + ex, y) and (x, y + ey) when exactly one
+            of them is live; otherwise (a corner) it takes the centre's value.
+        Wetting is set only by the adhesion term of Eq. 16, whose wall density
+        s is 1 at solid nodes (and outside a non-periodic edge) and 0 at fluid
+        and reservoir nodes."""
         p = self.p
         fluid = self._fluid(typ)
         res = self._reservoir(typ)
@@ -342,23 +347,29 @@ class Lattice:
         phi2 = np.where(live, phi2_of_rho1(r1, p["a0"], p["rho10"]), 0.0)
         s = np.where(live, 0.0, 1.0)
 
-        def wsum(field, neutral):
-            # sum_a w(|e_a|^2) field(x + e_a) e_a, a = 1..8.  With `neutral`, a
-            # solid neighbour contributes the centre node's own value (neutral
-            # wall: no net cohesion force from a wall, so w = 0 gives 90 deg).
+        def wsum(field):
+            # sum_a w(|e_a|^2) field(x + e_a) e_a, a = 1..8, a solid neighbour
+            # replaced by its mirror image as above
             sx = np.zeros_like(field)
             sy = np.zeros_like(field)
             for a in range(1, 9):
-                v = self.nb(field, EX9[a], EY9[a], 0.0)
-                if neutral:
-                    v = np.where(self.nb(live, EX9[a], EY9[a], False), v, field)
-                sx = sx + WF[a] * v * EX9[a]
-                sy = sy + WF[a] * v * EY9[a]
+                ex, ey = EX9[a], EY9[a]
+                v = self.nb(field, ex, ey, 0.0)
+                if ex != 0 and ey != 0:
+                    live_h = self.nb(live, ex, 0, False)
+                    live_v = self.nb(live, 0, ey, False)
+                    image = np.where(live_h & ~live_v, self.nb(field, ex, 0, 0.0),
+                                     np.where(live_v & ~live_h, self.nb(field, 0, ey, 0.0), field))
+                else:
+                    image = field
+                v = np.where(self.nb(live, ex, ey, False), v, image)
+                sx = sx + WF[a] * v * ex
+                sy = sy + WF[a] * v * ey
             return sx, sy
 
-        spx, spy = wsum(psi1, True)
-        s21x, s21y = wsum(phi2, True)   # neighbours' phi_2, for F_12
-        s12x, s12y = wsum(phi1, True)   # neighbours' phi_1, for F_21
+        spx, spy = wsum(psi1)
+        s21x, s21y = wsum(phi2)   # neighbours' phi_2, for F_12
+        s12x, s12y = wsum(phi1)   # neighbours' phi_1, for F_21
         sfull = self.nb(s, 0, 0, 1.0)
         ssx = np.zeros_like(s)
         ssy = np.zeros_like(s)

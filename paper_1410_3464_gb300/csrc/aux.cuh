@@ -76,15 +76,22 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
       const R j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
       R psc, p1c, p2c;
       potentials<R>(P, rho1, rho2, psc, p1c, p2c, status);
-      R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
+      // neighbours' potentials (live ones) first, then the stencils with a
+      // solid neighbour replaced by its mirror image across the wall, as in
+      // the bulk kernel
+      R nps[9], nq1[9], nq2[9];
+      bool nlv[9];
 #pragma unroll
       for (int a = 1; a < 9; ++a) {
         int xn, yn;
         const bool in = nbr(P, x, y, EX(a), EY(a), xn, yn);
         const long long nn = (long long)yn * P.nx + xn;
         const uint8_t tn = in ? (T[nn] & T_MASK) : T_WALL;
-        R ps = psc, q1 = p1c, q2 = p2c, sv = R(1);
-        if (is_live(tn)) {
+        nps[a] = psc;
+        nq1[a] = p1c;
+        nq2[a] = p2c;
+        nlv[a] = is_live(tn);
+        if (nlv[a]) {
           R a1, a2;
           if (is_fluid(tn)) {
             a1 = fshift<R>(P, 0, tn) + density_shifted<R>(F, N, nn);
@@ -96,15 +103,30 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
             a1 = R(u);
             a2 = R(v);
           }
-          potentials<R>(P, a1, a2, ps, q1, q2, status);
-          sv = R(0);
+          potentials<R>(P, a1, a2, nps[a], nq1[a], nq2[a], status);
+        }
+      }
+      R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
+#pragma unroll
+      for (int a = 1; a < 9; ++a) {
+        R ps = nps[a], q1 = nq1[a], q2 = nq2[a];
+        bool take = nlv[a];
+        if (EX(a) != 0 && EY(a) != 0 && !nlv[a]) {
+          const int ah = EX(a) > 0 ? 1 : 3, av = EY(a) > 0 ? 2 : 4;   // the axis links beside it
+          if (nlv[ah] != nlv[av]) {
+            const int m = nlv[ah] ? ah : av;
+            ps = nps[m];
+            q1 = nq1[m];
+            q2 = nq2[m];
+            take = true;
+          }
         }
         const R w = wf<R>(a);
         // differences from the centre value, in the bulk kernels' operation order
-        const R dp = sv == R(0) ? rsub<R>(ps, psc) : R(0);
-        const R d2 = sv == R(0) ? rsub<R>(q2, p2c) : R(0);
-        const R d1 = sv == R(0) ? rsub<R>(q1, p1c) : R(0);
-        const R vs = sv == R(0) ? R(0) : w;
+        const R dp = take ? rsub<R>(ps, psc) : R(0);
+        const R d2 = take ? rsub<R>(q2, p2c) : R(0);
+        const R d1 = take ? rsub<R>(q1, p1c) : R(0);
+        const R vs = nlv[a] ? R(0) : w;
         stencil_acc<R>(spx, w, dp, EX(a)); stencil_acc<R>(s2x, w, d2, EX(a));
         stencil_acc<R>(s1x, w, d1, EX(a)); stencil_add<R>(ssx, vs, EX(a));
         stencil_acc<R>(spy, w, dp, EY(a)); stencil_acc<R>(s2y, w, d2, EY(a));

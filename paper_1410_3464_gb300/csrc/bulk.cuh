@@ -495,10 +495,13 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   R mymax = R(-1.0 / 0.0);
   if (own && is_fluid(t)) {
     mymax = rho1;
-    // ---- forces (Eqs. 11, 14a/b, 16) with neutral solid neighbours.  The
-    // stencils sum w (value(x + e) - value(x)) e, equal to the sums of Eqs. 11
-    // and 14 since sum_a w e = 0, but free of the cancellation between nearly
-    // equal neighbour values in a bulk phase; a solid neighbour contributes 0.
+    // ---- forces (Eqs. 11, 14a/b, 16) with mirror-image solid neighbours.
+    // The stencils sum w (value(x + e) - value(x)) e, equal to the sums of
+    // Eqs. 11 and 14 since sum_a w e = 0, but free of the cancellation between
+    // nearly equal neighbour values in a bulk phase.  A solid neighbour takes
+    // its mirror image across the wall: the centre itself for an axis link (a
+    // zero difference), and for a diagonal link on a flat wall the live one of
+    // the two axis neighbours beside it (the centre at a corner).
     const Pot<R> pc = spot[eo];
     const R psc = pc.ps, p1c = pc.p1, p2c = pc.p2;
     // neighbour codes kept for the pushes: the low nibble of each of the eight
@@ -516,9 +519,22 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
       if (a < 5) abits |= unsigned((ca >> 5) & 0x3) << (2 * (a - 1));
       const bool lv = (ca & C_LIVE) != 0;
       const R w = wf<R>(a);
-      const R dp = lv ? rsub<R>(q.ps, psc) : R(0);
-      const R d2 = lv ? rsub<R>(q.p2, p2c) : R(0);
-      const R d1 = lv ? rsub<R>(q.p1, p1c) : R(0);
+      R vps = q.ps, vp1 = q.p1, vp2 = q.p2;
+      bool take = lv;
+      if (EX(a) != 0 && EY(a) != 0 && !lv) {
+        const Pot<R> qh = spot[eo + EX(a)];
+        const Pot<R> qv = spot[eo + EY(a) * SH::EXT_X];
+        const bool lh = (code_of<R>(qh.code) & C_LIVE) != 0, lw = (code_of<R>(qv.code) & C_LIVE) != 0;
+        if (lh != lw) {
+          vps = lh ? qh.ps : qv.ps;
+          vp1 = lh ? qh.p1 : qv.p1;
+          vp2 = lh ? qh.p2 : qv.p2;
+          take = true;
+        }
+      }
+      const R dp = take ? rsub<R>(vps, psc) : R(0);
+      const R d2 = take ? rsub<R>(vp2, p2c) : R(0);
+      const R d1 = take ? rsub<R>(vp1, p1c) : R(0);
       const R vs = lv ? R(0) : w;
       stencil_acc<R>(spx, w, dp, EX(a)); stencil_acc<R>(s2x, w, d2, EX(a));
       stencil_acc<R>(s1x, w, d1, EX(a)); stencil_add<R>(ssx, vs, EX(a));

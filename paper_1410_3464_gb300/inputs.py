@@ -21,6 +21,10 @@ D2Q5 transport with rest fraction J_0):
     (bubbles) in the pore space; species B, E, F transported, A derived from the
     liquid density; R1 (k1=1e-5, gas-producing), R3 (k3=1e-1), R2 on D(s)
     (k2=1e-3), R4 on D(s)/F(s) (k4=1e-3).
+  * beaker(): the paper's Section 5 scene (100x160, D(s) cylinder, free top
+    outlet), stand-in rates.
+  * droplet(): App. A2's static contact angle (201x201, a droplet on the
+    bottom wall, solid-fluid interaction w).
 """
 from __future__ import annotations
 
@@ -232,10 +236,9 @@ def beaker(nx=100, ny=160, grain=(50, 50, 15), level=100, k1=1e-5, r1_surface=10
     density (8.17, Eq. 13 domain limit 9.86) a liquid node that turns into F(s)
     hands its mass to two or three neighbours and pushes them out of the EOS
     domain, so k4 is slow (the paper's Fig. 9 also runs R4 at 1/10000 of its
-    rate), and the gas C(g) is light (M_C = 0.001 rho_l): a heavier gas
-    accumulates at the wall contact line.  Without reactions the scene runs
-    20,000 steps; with all four reactions on at these stand-in rates it still
-    diverges within 1,000 steps."""
+    rate), and the gas C(g) is light (M_C = 0.001 rho_l).  With all four
+    reactions on the scene runs 20,000 steps: the D(s) surface dissolves until
+    a shell of precipitated F(s) covers it (from about 2,500 steps on)."""
     y, x = np.mgrid[0:ny, 0:nx]
     gas = y >= level
     mask = np.where(gas, GAS, LIQUID).astype(np.uint8)
@@ -268,6 +271,34 @@ def beaker(nx=100, ny=160, grain=(50, 50, 15), level=100, k1=1e-5, r1_surface=10
     conc = np.zeros((4, ny, nx))
     conc[0][mask == LIQUID] = 1.0
     return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
+
+
+def droplet(nx=201, ny=201, radius=50.0, w=0.0, width=2.0):
+    """Static contact angle (App. A2): a semicircular liquid droplet of the
+    given radius centred on the bottom wall of an nx x ny domain with walls at
+    the top and bottom rows and periodic sides; rescaled C-S EOS at 0.65 T_c
+    (liquid 8.17 / gas 0.0537, density ratio about 150); tau = 1; no species.
+    The wall faces sit halfway between the wall rows and the first fluid rows
+    (y = 0.5 and y = ny - 1.5).  The solid-fluid interaction w of Eq. 16 acts
+    on the liquid component (w_1w = w); the gas component has none (w_2w = 0)."""
+    y, x = np.mgrid[0:ny, 0:nx]
+    xc, yw = (nx - 1) / 2.0, 0.5
+    r = np.hypot(x - xc, y - yw)
+    liq = 0.5 * (1.0 - np.tanh((r - radius) / width))
+    mask = np.where(liq > 0.5, LIQUID, GAS).astype(np.uint8)
+    mask[0, :] = WALL
+    mask[ny - 1, :] = WALL
+    rl, rg = 8.17, 0.0537
+    rho1 = rg + (rl - rg) * liq
+    rho2 = 0.05 + (1e-4 - 0.05) * liq
+    fluid = mask <= GAS
+    rho1 = np.where(fluid, rho1, 0.0)
+    rho2 = np.where(fluid, rho2, 0.0)
+    p = base_params(nx, ny)
+    p.update(periodic_x=1, periodic_y=0, eos_a=CS_RESCALED["eos_a"], eos_b=CS_RESCALED["eos_b"],
+             eos_R=CS_RESCALED["eos_R"], eos_T=0.65 * CS_RESCALED["Tc"], w_adh=(float(w), 0.0),
+             rho_ref=(rl, 1e-4), rho_ref_gas=(rg, 0.05))
+    return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=None, vol=None, params=p)
 
 
 def _log_uniform(u, lo, hi):

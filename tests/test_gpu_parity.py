@@ -251,6 +251,25 @@ def test_beaker_scene_free_top_outlet(pslbm):
     compare(got, ref, what="beaker")
 
 
+def test_beaker_runs_with_all_reactions(pslbm):
+    """The beaker with R1 (surface enhanced) to R4 on, 5000 steps on the FP64
+    and FP32 paths: no error, and the dissolving D(s) surface is passivated by
+    a shell of precipitated F(s) (R2 acts only on D(s) links; a D(s) node whose
+    V_D is gone but holds some V_F turns into F(s) rather than liquid), as in
+    the oracle, which shows the same shell (84 F(s) nodes, V_D = 625) from
+    2,500 steps on."""
+    for prec in (pslbm.FP64, pslbm.FP32):
+        sc = inputs.beaker()
+        with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                              precision=prec) as s:
+            s.step(5000)
+            f = s.read()
+        nF = int((f["type"] == 3).sum())
+        assert nF > 40, nF
+        assert 600.0 < f["vol"][0].sum() < 700.0
+        assert np.isfinite(f["rho1"]).all()
+
+
 def test_plain_scene_full_length_2000_steps(pslbm):
     """The plain-method scene for its full 2000 steps on the FP64 path.  The
     two sides differ only in rounding order (about 1e-16 per operation); the

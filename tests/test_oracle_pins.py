@@ -179,7 +179,7 @@ def test_adhesion_force_sign_and_magnitude():
     r1, r2, _, _ = L.moments()
     F1x, F1y, _, _ = L._forces(L.type, r1, r2, 0 * r1, 0 * r1)
     psi = lbm.psi1_of_rho(r1[1, 0], 1, 4, 1, p["eos_T"], -1.0)
-    # neutral wall: the cohesion sum of a uniform field is zero even beside the wall
+    # mirror-image wall: the cohesion sum of a uniform field is zero even beside the wall
     assert abs(F1y[1, 0] - 0.14 * psi * (1 / 9 + 2 / 36)) < 1e-15
     assert abs(F1y[2, 0]) < 1e-15
     assert np.all(np.abs(F1x) < 1e-15)
