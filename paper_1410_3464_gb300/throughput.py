@@ -1,7 +1,10 @@
 """Throughput of the FP32 path on the large-lattice and batched workloads.
 
     python -m paper_1410_3464_gb300.throughput --workload large --steps 300
-        porous discs 4096x2048 (seed 1), one simulation
+        porous discs 4096x2048 (seed 4), one simulation.  At this size the
+        seeded scenes leave the EOS domain after a few hundred to a few
+        thousand steps (seed 4 lasts longest, past 2,250 steps), so the run is
+        a throughput measurement of 340 steps, not a long simulation
     python -m paper_1410_3464_gb300.throughput --workload plain --steps 2000
         the plain-method scene (128x64, one grain, one bubble, 2 species), FP64
     python -m paper_1410_3464_gb300.throughput --workload porous-fp64 --steps 300
@@ -138,7 +141,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=300)
     args = ap.parse_args(argv)
     if args.seed is None:
-        args.seed = 1 if args.workload == "large" else 4
+        args.seed = 4
     if args.workload == "large":
         out = large(args)
     elif args.workload == "batch":
