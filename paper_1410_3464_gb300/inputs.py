@@ -25,6 +25,8 @@ D2Q5 transport with rest fraction J_0):
     outlet), stand-in rates.
   * droplet(): App. A2's static contact angle (201x201, a droplet on the
     bottom wall, solid-fluid interaction w).
+  * fracture(): App. C's dissolving fracture (100x90, aperture 30 between two
+    D(s) blocks, pressure-driven single-phase flow, R2 at the walls).
 """
 from __future__ import annotations
 
@@ -299,6 +301,41 @@ def droplet(nx=201, ny=201, radius=50.0, w=0.0, width=2.0):
              eos_R=CS_RESCALED["eos_R"], eos_T=0.65 * CS_RESCALED["Tc"], w_adh=(float(w), 0.0),
              rho_ref=(rl, 1e-4), rho_ref_gas=(rg, 0.05))
     return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=None, vol=None, params=p)
+
+
+def fracture(L=100, H=90, h0=30, k2=1e-4, overpressure=1.001, conc_in=1.0, rho2_liq=2e-5):
+    """Fracture dissolution (App. C): an aperture-h0 fracture between two D(s)
+    blocks in an L x H medium.  Walls on the top and bottom rows (no slip); a
+    fixed-density inlet reservoir column before the medium (liquid at
+    `overpressure` times the coexistence density) and an outlet column after
+    it at the coexistence density, so the flow is pressure driven; one phase
+    (liquid everywhere), original C-S EOS at 0.7 T_c, tau = 1.  The only species
+    B enters at conc_in and dissolves the fracture walls by R2 (first order,
+    C_sat = 0; J0 = 1/3, tau_g = 0.8).  The blocks' faces toward the reservoirs
+    touch no liquid, so, as in the paper, they do not react; a small k2 keeps
+    the dissolution uniform along the fracture."""
+    nx, ny = L + 2, H
+    y, x = np.mgrid[0:ny, 0:nx]
+    lo = (H - h0) // 2
+    mask = np.full((ny, nx), LIQUID, np.uint8)
+    mask[(y < lo) | (y >= lo + h0)] = SOLID_D
+    mask[0, :] = WALL
+    mask[ny - 1, :] = WALL
+    mask[1:ny - 1, 0] = INLET
+    mask[1:ny - 1, nx - 1] = OUTLET
+    rl = COEX_ORIGINAL_07[0]
+    fluid = mask == LIQUID
+    rho1 = np.where(fluid, rl, 0.0)
+    rho2 = np.where(fluid, rho2_liq, 0.0)
+    p = base_params(nx, ny)
+    p.update(periodic_x=0, periodic_y=0, rho_ref=(rl, rho2_liq),
+             n_species=1, idx_A=IDX_ABSENT, idx_B=0, idx_E=IDX_ABSENT, idx_F=IDX_ABSENT,
+             J0=_pad([1.0 / 3.0]), tau_g=_pad([0.8], 1.0), conc_ref=_pad([0.0]),
+             k2=k2, Vbar_D=1.0, Vbar_F=1.0, V_split=2.0, seed=11,
+             rho_in_liq=(overpressure * rl, rho2_liq), rho_in_gas=(overpressure * rl, rho2_liq),
+             rho_out=(rl, rho2_liq), rho_out_gas=(rl, rho2_liq), conc_in=_pad([conc_in]))
+    conc = np.zeros((1, ny, nx))
+    return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
 
 
 def _log_uniform(u, lo, hi):
