@@ -25,6 +25,7 @@ from scipy.integrate import quad
 from scipy.optimize import brentq
 
 from oracle import lbm
+from paper_1410_3464_gb300 import inputs
 
 A, B, R = 1.0, 4.0, 1.0
 T = 0.7 * 0.0943294
@@ -142,3 +143,20 @@ def test_laplace_law_static_droplet():
     assert slope > 0                         # positive surface tension
     assert r2 > 0.999
     assert abs(icpt) < 0.05 * a[:, 1].max()
+
+
+def test_wall_without_interaction_rests_at_ninety_degrees():
+    """App. A2 and Section 5: a wall without solid-fluid interaction (w = 0)
+    holds a droplet at 90 degrees.  Oracle, 41x31, droplet r = 10 on the bottom
+    wall, 1500 steps (the angle is settled by then: 3000 steps give the same to
+    0.1 degree); the circle fit of the rho_1 midpoint contour gives 86.8 degrees
+    at this small radius (the 201x201 GPU runs give 89.4-89.7).  A reading in
+    which every solid neighbour takes the centre node's own value gives about
+    64 degrees."""
+    from paper_1410_3464_gb300 import contact_angle as ca
+    sc = inputs.droplet(nx=41, ny=31, radius=10.0, w=0.0)
+    L = lbm.Lattice(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], None, None)
+    L.run(1500)
+    r1 = L.moments()[0]
+    out = ca.contact_angle(np.where(L._fluid(L.type), r1, 0.0), skip=3)
+    assert abs(out["theta_deg"] - 90.0) < 5.0, out
