@@ -81,7 +81,10 @@ typedef struct {
     double tau[2];                 /* BGK relaxation times (> 0.5), liquid and gas component */
     double G11, G12, G21;          /* Eq. 11 cohesion (G22 = 0), Eq. 14 cross interactions */
     double a0, rho10, rho20;       /* Eq. 15 constants */
-    double w_adh[2];               /* Eq. 16 fluid-solid interaction strengths */
+    double w_adh[2];               /* Eq. 16 fluid-solid interaction strengths; with 0 a wall
+                                      holds a 90-degree contact angle (solid neighbours enter
+                                      the Eq. 11 and 14 sums as their mirror images across the
+                                      wall), below 0 it wets */
     double eos_a, eos_b, eos_R, eos_T; /* Eq. 12 Carnahan-Starling constants and temperature */
     double body_force[2];          /* optional uniform acceleration (x, y) */
     double rho_ref[2];             /* reference densities of the liquid phase: FP32 population
