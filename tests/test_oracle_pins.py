@@ -185,6 +185,31 @@ def test_adhesion_force_sign_and_magnitude():
     assert np.all(np.abs(F1x) < 1e-15)
 
 
+def test_flat_wall_is_a_mirror_for_the_cohesion_sums():
+    """Walls are 90-degree walls (App. A2, Section 5): in the Eq. 11 and 14 sums
+    a solid neighbour takes its mirror image across a flat wall, so next to a
+    flat wall a field that varies along the wall but not across it feels no
+    wall-normal cohesion force, exactly as far from the wall.  (Taking the
+    centre node's own value for the diagonal wall neighbours would leave
+    w(2) (psi(x+1, 2) + psi(x-1, 2) - 2 psi(x, 1)) in the normal sum.)"""
+    nx, ny = 16, 8
+    p = lbm.default_params(nx, ny)
+    p.update(periodic_x=1, periodic_y=0, G12=0.0, G21=0.0, w_adh=(0.0, 0.0))
+    m = uniform_mask(nx, ny)
+    m[0, :] = lbm.WALL
+    m[ny - 1, :] = lbm.WALL
+    x = np.arange(nx)
+    # a density varying along x only (periodic), inside the EOS domain
+    rho1 = np.tile(0.30 + 0.04 * np.sin(2 * np.pi * x / nx), (ny, 1))
+    L = _lattice_with_density(rho1, np.full((ny, nx), 1e-3), p, m)
+    r1, r2, _, _ = L.moments()
+    F1x, F1y, _, _ = L._forces(L.type, r1, r2, 0 * r1, 0 * r1)
+    assert np.all(np.abs(F1y[1:ny - 1]) < 1e-15)
+    # the force along the wall is the bulk one on every fluid row
+    np.testing.assert_allclose(F1x[1], F1x[ny // 2], rtol=0, atol=1e-15)
+    assert np.abs(F1x[ny // 2]).max() > 1e-4
+
+
 # ---------------------------------------------------------------- flow
 
 def test_closed_domain_mass_conservation():
