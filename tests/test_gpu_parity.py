@@ -251,6 +251,16 @@ def test_beaker_scene_free_top_outlet(pslbm):
     compare(got, ref, what="beaker")
 
 
+@pytest.mark.parametrize("w", [-0.2, 0.0])
+def test_droplet_contact_line(pslbm, w):
+    """A droplet on a flat wall (App. A2 scene, 48x32, r = 10, rescaled C-S EOS):
+    the mirror-image wall in the cohesion sums and the Eq. 16 adhesion at the
+    contact line, 150 steps on the FP64 path against the oracle."""
+    sc = inputs.droplet(nx=48, ny=32, radius=10.0, w=w)
+    got, ref, _ = run_both(pslbm, sc, 150)
+    compare(got, ref, what=f"droplet w={w}")
+
+
 def test_beaker_runs_with_all_reactions(pslbm):
     """The beaker with R1 (surface enhanced) to R4 on, 5000 steps on the FP64
     and FP32 paths: no error, and the dissolving D(s) surface is passivated by
