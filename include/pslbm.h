@@ -236,21 +236,24 @@ const char* pslbm_last_error(pslbm_t h);
 /* Budget of the current state written to DEVICE memory without allocating
  * anything.  The paper has no counterpart: this entry point exists for callers
  * that must not allocate device memory at the moment they want the budget --
- * code running while a CUDA graph is being captured (cudaMalloc is not allowed
- * there), hosts that give the library a fixed memory pool and forbid later
- * allocation, real-time loops where an allocation could stall.
+ * hosts that give the library a fixed memory pool and forbid any later
+ * allocation, and real-time loops where an allocation (which can synchronise
+ * the device or wait on a driver lock) could stall.
  *   out  caller-owned device buffer of 6 + n_species doubles; receives the
  *        PSLBM_F_BUDGET layout (max rho1, sum rho1, sum rho2, sum C_k, sum V_D,
- *        sum V_F, step count), the same numbers as pslbm_read_fields gives.
+ *        sum V_F, step count), bit for bit the numbers pslbm_read_fields gives
+ *        (same reduction grid, same order of additions).
  * Asynchronous on the library stream.  The per-block partial sums live in one
- * file-scope device array of 4096 x 9 doubles (288 KiB), held by every GPU that
- * loads the library until the process exits; lattices above 4096 * 8192 =
- * 33,554,432 nodes are rejected with PSLBM_ERR_PARAM.  Every call overwrites
- * the rows it reads, so nothing has to be cleared between calls, but all calls
- * share the array: calls that overlap on the GPU (other streams, other threads)
- * race.  The first call on each device looks up the array's device address
- * (with that device current); make that first call before any stream capture.
- * Calls no cudaMalloc, cudaFree or allocating library routine. */
+ * file-scope device array of 512 x 9 doubles (36 KiB), held by every GPU that
+ * loads the library until the process exits; each of the 512 rows covers a
+ * contiguous 1/512 of the lattice, so every lattice the library accepts fits
+ * (up to 100,000,000 nodes) and no size is rejected.  Every call overwrites all
+ * 512 rows before it reads them, so nothing has to be cleared between calls,
+ * but all calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race.  The first call on each device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  Returns the handle's sticky error, if any, without
+ * launching.  Calls no cudaMalloc, cudaFree or allocating library routine. */
 pslbm_status pslbm_budget_device_noalloc(pslbm_t h, double* out);
 
 /* ---------------------------------------------------------------- batching

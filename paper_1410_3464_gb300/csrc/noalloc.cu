@@ -3,11 +3,11 @@
 // pslbm_read_fields(PSLBM_F_BUDGET) reduces the state into per-block partial
 // sums held in a device buffer the library allocates on first use.  Some
 // callers cannot allocate device memory at the point where they want the
-// budget: code running while a CUDA graph is being captured (cudaMalloc is not
-// allowed there), hosts that hand the library a fixed memory pool and forbid
-// further allocation, and real-time loops where an allocation may stall.
-// pslbm_budget_device_noalloc gives them the same numbers with the partial
-// sums in a file-scope device array instead.
+// budget: hosts that hand the library a fixed memory pool and forbid any later
+// allocation, and real-time loops where an allocation (which may synchronise
+// the device or take a driver lock) could stall.  pslbm_budget_device_noalloc
+// gives them the same numbers with the partial sums in a file-scope device
+// array instead.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -21,15 +21,13 @@ using namespace pslbm;
 
 namespace {
 
-// Scratch limit: one partial-sum row per block of up to 8192 nodes, at most
-// 4096 blocks, so lattices of up to 4096 * 8192 = 33,554,432 nodes.  The array
-// is 4096 * NBUD doubles (288 KiB) and every GPU that loads the library holds it
-// until the process exits.
-constexpr int NOALLOC_NODES_PER_BLOCK = 8192;
-constexpr int NOALLOC_MAX_BLOCKS = 4096;
-constexpr long long NOALLOC_MAX_NODES = (long long)NOALLOC_NODES_PER_BLOCK * NOALLOC_MAX_BLOCKS;
-
-static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_BLOCKS * NBUD];
+// Scratch: one partial-sum row per block of the budget reduction, with the
+// same fixed grid of BUD_BLOCKS blocks that pslbm_read_fields uses, so both
+// add the same numbers in the same order and give the same bits.  Each block
+// covers a contiguous 1/BUD_BLOCKS of the lattice, so any lattice the library
+// accepts fits.  The array is BUD_BLOCKS * NBUD doubles (36 KiB), held by every
+// GPU that loads the library until the process exits.
+static __device__ __align__(256) double g_noalloc_partials[BUD_BLOCKS * NBUD];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mu;
@@ -54,18 +52,18 @@ __global__ void __launch_bounds__(BUD_FINAL_THREADS) k_noalloc_final(const doubl
 }
 
 template <class TF, class TG, class R, int NS>
-void launch_partial(cudaStream_t s, int nblocks, const DevInst* I, double* part) {
-  k_budget_partial<TF, TG, R, NS><<<nblocks, BUD_THREADS, 0, s>>>(I, part);
+void launch_partial(cudaStream_t s, const DevInst* I, double* part) {
+  k_budget_partial<TF, TG, R, NS><<<BUD_BLOCKS, BUD_THREADS, 0, s>>>(I, part);
 }
 
 template <class TF, class TG, class R>
-bool dispatch_ns(int ns, cudaStream_t s, int nblocks, const DevInst* I, double* part) {
+bool dispatch_ns(int ns, cudaStream_t s, const DevInst* I, double* part) {
   switch (ns) {
-    case 0: launch_partial<TF, TG, R, 0>(s, nblocks, I, part); return true;
-    case 1: launch_partial<TF, TG, R, 1>(s, nblocks, I, part); return true;
-    case 2: launch_partial<TF, TG, R, 2>(s, nblocks, I, part); return true;
-    case 3: launch_partial<TF, TG, R, 3>(s, nblocks, I, part); return true;
-    case 4: launch_partial<TF, TG, R, 4>(s, nblocks, I, part); return true;
+    case 0: launch_partial<TF, TG, R, 0>(s, I, part); return true;
+    case 1: launch_partial<TF, TG, R, 1>(s, I, part); return true;
+    case 2: launch_partial<TF, TG, R, 2>(s, I, part); return true;
+    case 3: launch_partial<TF, TG, R, 3>(s, I, part); return true;
+    case 4: launch_partial<TF, TG, R, 4>(s, I, part); return true;
   }
   return false;
 }
@@ -93,38 +91,36 @@ cudaError_t partials_address(double** out) {
 namespace pslbm {
 // Accessors into the handle (defined in runtime.cu).
 const DevInst* handle_device_inst(pslbm_t h);
-long long handle_nodes(pslbm_t h);
 int handle_precision(pslbm_t h);
 int handle_species(pslbm_t h);
+pslbm_status handle_sticky(pslbm_t h);
 pslbm_status handle_fail(pslbm_t h, pslbm_status s, const std::string& msg);
 cudaStream_t library_stream();
 }  // namespace pslbm
 
 extern "C" pslbm_status pslbm_budget_device_noalloc(pslbm_t h, double* out) {
   if (!h) return handle_fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
+  // a handle whose state is poisoned (device error, non-finite or EOS-domain
+  // state, timed-out wait) reports that error, as every other call does
+  const pslbm_status sticky = handle_sticky(h);
+  if (sticky != PSLBM_OK) return sticky;
   if (!out) return handle_fail(h, PSLBM_ERR_PARAM, "out is NULL");
-  const long long N = handle_nodes(h);
-  if (N > NOALLOC_MAX_NODES)
-    return handle_fail(h, PSLBM_ERR_PARAM,
-                       "lattice has " + std::to_string(N) + " nodes; the allocation-free budget supports at most " +
-                           std::to_string(NOALLOC_MAX_NODES));
   double* part = nullptr;
   cudaError_t e = partials_address(&part);
   if (e != cudaSuccess)
     return handle_fail(h, PSLBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-  const int nblocks = (int)((N + NOALLOC_NODES_PER_BLOCK - 1) / NOALLOC_NODES_PER_BLOCK);
   cudaStream_t s = library_stream();
   const DevInst* I = handle_device_inst(h);
   const int ns = handle_species(h);
   bool ok = false;
   switch (handle_precision(h)) {
-    case PSLBM_FP64: ok = dispatch_ns<double, double, double>(ns, s, nblocks, I, part); break;
-    case PSLBM_FP32: ok = dispatch_ns<float, float, float>(ns, s, nblocks, I, part); break;
-    case PSLBM_FP32_SOLUTE_F16: ok = dispatch_ns<float, __half, float>(ns, s, nblocks, I, part); break;
-    case PSLBM_FP32_SOLUTE_BF16: ok = dispatch_ns<float, __nv_bfloat16, float>(ns, s, nblocks, I, part); break;
+    case PSLBM_FP64: ok = dispatch_ns<double, double, double>(ns, s, I, part); break;
+    case PSLBM_FP32: ok = dispatch_ns<float, float, float>(ns, s, I, part); break;
+    case PSLBM_FP32_SOLUTE_F16: ok = dispatch_ns<float, __half, float>(ns, s, I, part); break;
+    case PSLBM_FP32_SOLUTE_BF16: ok = dispatch_ns<float, __nv_bfloat16, float>(ns, s, I, part); break;
   }
   if (!ok) return handle_fail(h, PSLBM_ERR_PARAM, "no budget kernel for this precision / species count");
-  k_noalloc_final<<<1, BUD_FINAL_THREADS, 0, s>>>(part, nblocks, ns, I, out);
+  k_noalloc_final<<<1, BUD_FINAL_THREADS, 0, s>>>(part, BUD_BLOCKS, ns, I, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return handle_fail(h, PSLBM_ERR_CUDA, std::string("budget launch: ") + cudaGetErrorString(e));
   return PSLBM_OK;

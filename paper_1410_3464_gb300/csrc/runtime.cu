@@ -1183,6 +1183,7 @@ const DevInst* handle_device_inst(pslbm_t h) { return h->d; }
 long long handle_nodes(pslbm_t h) { return h->N; }
 int handle_precision(pslbm_t h) { return h->prec; }
 int handle_species(pslbm_t h) { return h->ns; }
+pslbm_status handle_sticky(pslbm_t h) { return h->sticky; }
 pslbm_status handle_fail(pslbm_t h, pslbm_status s, const std::string& msg) { return fail(h, s, msg); }
 cudaStream_t library_stream() { return lib_stream(); }
 }  // namespace pslbm

@@ -200,7 +200,16 @@ pslbm_status pslbm_server_advance(pslbm_server_t s, int32_t* n_active, int32_t* 
       continue;
     }
     std::vector<double> b;
-    if (read_budget(s, r, b) == PSLBM_OK) r->v0 = b[3 + r->p.n_species] + b[4 + r->p.n_species];
+    if (read_budget(s, r, b) != PSLBM_OK) {
+      // without the initial solid volume the stop criterion cannot run: the
+      // request fails alone
+      r->state = PSLBM_REQ_FAILED;
+      r->error = std::string("initial budget read failed: ") + pslbm_last_error(r->h);
+      pslbm_destroy(r->h);
+      r->h = nullptr;
+      continue;
+    }
+    r->v0 = b[3 + r->p.n_species] + b[4 + r->p.n_species];
     s->used += r->bytes;
     r->state = PSLBM_REQ_ACTIVE;
     s->active.push_back(r);
@@ -248,7 +257,18 @@ pslbm_status pslbm_server_advance(pslbm_server_t s, int32_t* n_active, int32_t* 
     if (hs != PSLBM_OK) return sfail(s, hs, pslbm_last_error(r->h));
     std::vector<double> b;
     pslbm_status st = read_budget(s, r, b);
-    if (st != PSLBM_OK) return sfail(s, st, "budget read failed");
+    if (st != PSLBM_OK) {
+      // a request whose budget cannot be read fails alone; the others go on
+      if (!s->dirty) drop_batches(s);
+      s->dirty = true;
+      r->error = std::string("budget read failed: ") + pslbm_last_error(r->h);
+      pslbm_destroy(r->h);
+      r->h = nullptr;
+      s->used -= r->bytes;
+      r->state = PSLBM_REQ_FAILED;
+      ++done_now;
+      continue;
+    }
     r->steps_done = (int64_t)b.back();
     const double v = b[3 + r->p.n_species] + b[4 + r->p.n_species];
     const bool by_budget = r->steps_done >= r->step_budget;
