@@ -1,26 +1,35 @@
 #!/usr/bin/env python
 """Throughput benchmark of the reactive two-phase LBM step on GB300.
 
-Workload: the porous-medium reactive two-phase lattice (1024x512, seeded
-overlapping D(s) discs of radius 8-24 at porosity 0.6, liquid inflow from an
-inlet reservoir, phase-following outlet reservoir, seeded gas slugs in the
-pores, species B, E, F transported and A derived, R1-R4), FP32 compute with
-shifted FP32 storage.  One step is one pass
-of the whole hot path: the fused bulk kernel, the VOP kernel and the
-amendment kernel.
+Workloads (--workload):
+  batch (default)  256 independent porous geometries stepped together as one
+                   batch: sides log-uniform 128-1024 (multiples of 16),
+                   porosity U[0.4, 0.8], reaction rates log-uniform 1e-6-1e-1,
+                   seeded gas bubbles, inlet/outlet reservoirs, species B, E, F
+                   transported and A derived, FP32 (48.5 M nodes, 14.6 GB of
+                   device state, far larger than L2).  With N ranks the trace
+                   holds 256 N requests and every rank takes its own 256.
+  porous           one porous lattice 1024x512 (seed 1), the same physics; its
+                   state (about 150 MB) is near the L2 size, so L2 is flushed
+                   (256 MiB write) before every timed step.
+  large            one porous lattice 4096x2048 (seed 4).
 
-Prints one JSON line (rank 0).  Metric: MLUPS (all lattice nodes x steps / s,
-whole job).  L2 is flushed (256 MiB write) before every timed step; each step
-is timed with CUDA events on the library stream.
+One step is one pass of the whole hot path: the fused bulk kernel, the VOP
+kernel and the amendment kernel, over every node of every member.  Each timed
+step is bracketed per kernel by CUDA events on the library stream.  Prints one
+JSON line (rank 0).  Metric: MLUPS (all lattice nodes x steps / s, whole job).
 
---impl reference times the CPU oracle on a bounded sample of the same
-workload (256x128, same generator) on the host cores.
+--impl reference times the CPU oracle (plain numpy FP64) on the host cores on a
+bounded sample of the same workload: small members of the same request trace,
+one per worker process, each advanced --warmup + --steps oracle steps.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,24 +42,33 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(nx=1024, ny=512, seed=1)
-SAMPLE = dict(nx=256, ny=128, seed=1)
-WORKLOAD_NAME = ("porous discs 1024x512 (radii 8-24, porosity 0.6, seed 1), pressure-driven liquid inflow "
-                 "(inlet 1% over coexistence, phase-following outlet), seeded gas slugs in the pores, "
-                 "species B,E,F transported + A derived, R1-R4 (k1=1e-5, k3=1e-1, k2=1e-3, k4=1e-3)")
-PROFILE_JSON = os.path.join(ROOT, "profiles", "k_bulk_porous1024x512_fp32.json")
+BATCH = dict(instances=256, seed=4, size_range=(128, 1024), budget_range=(1000, 10000), rate_range=(1e-6, 1e-1),
+             porosity_range=(0.4, 0.8))
+SINGLES = {"porous": dict(nx=1024, ny=512, seed=1), "large": dict(nx=4096, ny=2048, seed=4)}
+PHYSICS = ("pressure-driven liquid inflow (inlet reservoir over coexistence, phase-following outlet), seeded gas "
+           "bubbles in the pores, species B,E,F transported + A derived, R1-R4")
+WORKLOAD_NAMES = {
+    "batch": ("256 porous geometries in one batch (request trace seed 4): sides log-uniform 128-1024 (multiples of "
+              "16), porosity U[0.4,0.8], rates k1,k3,k2,k4 log-uniform 1e-6-1e-1 (k1 capped at 1e-4), " + PHYSICS),
+    "porous": "porous discs 1024x512 (radii 8-24, porosity 0.6, seed 1), " + PHYSICS + " (k1=1e-5, k3=1e-1, k2=k4=1e-3)",
+    "large": "porous discs 4096x2048 (radii 8-24, porosity 0.6, seed 4), " + PHYSICS + " (k1=1e-5, k3=1e-1, k2=k4=1e-3)",
+}
+# oracle sample: members of the same trace with both sides at most this long
+SAMPLE_SIDE = 256
 STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma 1-stage"}
+PROFILE_TAGS = {"batch": "batch256", "porous": "porous1024x512", "large": "porous4096x2048"}
 KERNEL_NAMES = {0: "k_bulk", 1: "k_bulk_tma<2 stages>", 2: "k_bulk_tma<1 stage>"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["batch", "porous", "large"], default="batch")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_f16", "fp32_bf16"], default="fp32")
-    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline and e2e legs")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline and the e2e leg")
     return ap.parse_args()
 
 
@@ -110,13 +128,38 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ CPU oracle
+# ------------------------------------------------------------------ workloads
 
-def oracle_run(seconds_budget, max_steps=None, warmup=1):
-    """Time the CPU oracle on the bounded sample; returns (MLUPS, steps, seconds)."""
-    from oracle import lbm
+def batch_requests(rank=0, world=1):
+    from paper_1410_3464_gb300 import inputs, replicas
+    reqs = inputs.request_stream(BATCH["instances"] * world, seed=BATCH["seed"], size_range=BATCH["size_range"],
+                                 budget_range=BATCH["budget_range"], rate_range=BATCH["rate_range"],
+                                 porosity_range=BATCH["porosity_range"], stop_fraction=0.0)
+    return replicas.share(reqs, rank, world)
+
+
+def oracle_sample(workload, count):
+    """The bounded CPU sample of a workload: `count` scene descriptions the
+    oracle workers build themselves."""
+    if workload == "batch":
+        small = [r for r in batch_requests() if r["nx"] <= SAMPLE_SIDE and r["ny"] <= SAMPLE_SIDE]
+        return [("request", r) for r in small[:count]]
+    seed = SINGLES[workload]["seed"]
+    return [("porous", dict(nx=256, ny=128, seed=seed))] * count
+
+
+def _build_scene(desc):
     from paper_1410_3464_gb300 import inputs
-    sc = inputs.porous_discs(**SAMPLE)
+    kind, d = desc
+    return inputs.request_scene(d) if kind == "request" else inputs.porous_discs(**d)
+
+
+def _oracle_worker(desc, warmup, steps, seconds):
+    """One oracle process: build the scene, run `warmup` steps, then `steps`
+    timed steps (or as many as fit in `seconds` when steps is None).
+    Returns (nodes, timed steps, elapsed seconds)."""
+    from oracle import lbm
+    sc = _build_scene(desc)
     L = lbm.Lattice(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"])
     for _ in range(warmup):
         L.step()
@@ -126,15 +169,49 @@ def oracle_run(seconds_budget, max_steps=None, warmup=1):
         L.step()
         n += 1
         el = time.perf_counter() - t0
-        if (max_steps is not None and n >= max_steps) or (max_steps is None and el >= seconds_budget):
+        if (steps is not None and n >= steps) or (steps is None and el >= seconds):
             break
-    nodes = SAMPLE["nx"] * SAMPLE["ny"]
-    return nodes * n / el / 1e6, n, el
+    return int(sc["mask"].size), n, el
 
 
-def sample_desc(n, el):
-    return (f"CPU oracle (numpy FP64, one thread) on the same generator at {SAMPLE['nx']}x{SAMPLE['ny']} "
-            f"(seed {SAMPLE['seed']}): {n} steps in {el:.1f} s")
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_pool_run(workload, workers, warmup, steps, seconds):
+    """Run the oracle on `workers` host processes at once (spawned, one numpy
+    thread each); returns (MLUPS over all workers, total node-steps, wall s, sample text)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    descs = oracle_sample(workload, workers)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(descs)) as pool:
+        res = pool.starmap(_oracle_worker, [(d, warmup, steps, seconds) for d in descs])
+    node_steps = sum(nodes * n for nodes, n, _ in res)
+    wall = max(el for _, _, el in res)
+    sizes = sorted({f"{d[1]['nx']}x{d[1]['ny']}" for d in descs})
+    text = (f"CPU oracle (numpy FP64) in {len(descs)} process(es), one per scene, on "
+            f"{'members of the same request trace with both sides <= %d' % SAMPLE_SIDE if workload == 'batch' else 'a 256x128 lattice of the same generator'}"
+            f" ({', '.join(sizes[:6])}{', ...' if len(sizes) > 6 else ''}): {warmup} warm-up step(s), then "
+            f"{min(n for _, n, _ in res)}-{max(n for _, n, _ in res)} timed steps per scene in {wall:.1f} s")
+    return node_steps / wall / 1e6, node_steps, wall, text
+
+
+def cpu_baseline(workload):
+    """The oracle on one host core and on all host cores, about 10 s each."""
+    ncores = os.cpu_count() or 1
+    one, _, _, one_text = oracle_pool_run(workload, 1, 1, None, 10.0)
+    allc, _, _, all_text = oracle_pool_run(workload, ncores, 1, None, 10.0)
+    return {"value": allc, "unit": "MLUPS", "cores": ncores, "kind": "oracle", "sample": all_text,
+            "single_thread": {"value": one, "unit": "MLUPS", "cores": 1, "sample": one_text},
+            "cpu_model": cpu_model(), "nproc": ncores}
 
 
 # ------------------------------------------------------------------ arms
@@ -144,23 +221,47 @@ def reference_arm(args):
     ws, rank, _ = replicas.env()
     if rank != 0:
         return 0
-    mlups_w, _, _ = oracle_run(0, max_steps=max(1, args.warmup), warmup=0)
-    mlups, n, el = oracle_run(0, max_steps=args.steps, warmup=0)
+    ncores = os.cpu_count() or 1
+    mlups, node_steps, wall, text = oracle_pool_run(args.workload, ncores, max(1, args.warmup), args.steps, None)
     line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD_NAME, "sample": f"{SAMPLE['nx']}x{SAMPLE['ny']}"},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": sample_desc(n, el)},
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD_NAMES[args.workload], "sample": text},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": ncores, "kind": "oracle", "sample": text,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def algorithmic_bytes(types, ns, fs, gs):
+    """Bulk-kernel bytes of one step: every population of a fluid node read and
+    written once (2 x 18 x fs), every solute population of a liquid node read and
+    written once (2 x 5 ns x gs), one type byte read and written per node."""
+    n_fluid = int((types <= 1).sum())
+    n_liq = int((types == 0).sum())
+    return n_fluid * 36 * fs + n_liq * 10 * ns * gs + 2 * types.size, n_fluid, n_liq
+
+
+def profile_traffic(workload, variant):
+    """DRAM bytes per bulk launch from the committed ncu summary of the same
+    kernel variant built from the same device sources (None otherwise)."""
+    from paper_1410_3464_gb300 import profile_case
+    path = os.path.join(ROOT, "profiles", f"k_bulk_{PROFILE_TAGS[workload]}_fp32.json")
+    if not os.path.exists(path):
+        return None
+    pj = json.load(open(path))
+    if pj.get("source_hash") != profile_case.kernel_source_hash():
+        return None
+    return pj.get("traffic_per_launch", {}).get(variant)
+
+
 def ours_arm(args):
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
     import torch
 
-    from paper_1410_3464_gb300 import inputs, profile_case, pslbm, replicas
+    from paper_1410_3464_gb300 import inputs, pslbm, replicas
 
     ws, rank, local = replicas.env()
     replicas.init(ws)
@@ -169,34 +270,50 @@ def ours_arm(args):
             "fp32_bf16": pslbm.FP32_SOLUTE_BF16}[args.precision]
     fs = 8 if prec == pslbm.FP64 else 4
     gs = {pslbm.FP64: 8, pslbm.FP32: 4}.get(prec, 2)
-    sc = inputs.porous_discs(**WORKLOAD)
-    N = WORKLOAD["nx"] * WORKLOAD["ny"]
-    ns = sc["params"]["n_species"]
-
     stream = torch.cuda.ExternalStream(pslbm.get_stream())
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    sim = pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"], precision=prec)
-    # kernel variant (tile shape x staging) chosen under the timed loop's own
-    # conditions (L2 flushed before every step): a few steps of each
-    trials = {}
-    stagings = [0, 1, 2] if sim.staging()[1] else [0]
-    with torch.cuda.stream(stream):
-        for shape in ((16, 16), (32, 8)):
-            for sg in stagings:
-                sim.set_tile_shape(*shape)
-                sim.set_staging(sg)
-                ts = []
-                for _ in range(5):
-                    flush.zero_()
-                    ts.append(sim.profile_step(1)[1])
-                trials[(shape, sg)] = statistics.median(ts[1:])
+    batch = args.workload == "batch"
+    if batch:
+        scenes = [inputs.request_scene(r) for r in batch_requests(rank, ws)]
+    else:
+        scenes = [inputs.porous_discs(**SINGLES[args.workload])]
+    N = sum(int(sc["mask"].size) for sc in scenes)
+    ns = scenes[0]["params"]["n_species"]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda") if args.workload == "porous" else None
+
+    def make_sims():
+        return [pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                                 precision=prec) for sc in scenes]
+
+    sims = make_sims()
+    trials = None
+    if batch:
+        runner = pslbm.Batch(sims)
+        runner.step(30)              # variant autotuning (6 variants x 4 steps) and a first warm-up
+    else:
+        # one lattice: each variant timed for 5 steps under the timed loop's own
+        # conditions (L2 flushed before every step for the 1024x512 lattice)
+        runner = sims[0]
+        trials = {}
+        stagings = [0, 1, 2] if runner.staging()[1] else [0]
+        with torch.cuda.stream(stream):
+            for shape in ((16, 16), (32, 8)):
+                for sg in stagings:
+                    runner.set_tile_shape(*shape)
+                    runner.set_staging(sg)
+                    ts = []
+                    for _ in range(5):
+                        if flush is not None:
+                            flush.zero_()
+                        ts.append(runner.profile_step(1)[1])
+                    trials[(shape, sg)] = statistics.median(ts[1:])
         torch.cuda.synchronize()
-    best = min(trials, key=trials.get)
-    sim.set_tile_shape(*best[0])
-    sim.set_staging(best[1])
-    t = sim.read(pslbm.F_TYPE)["type"]
-    n_fluid = int((t <= 1).sum())
-    n_liq = int((t == 0).sum())
+        best = min(trials, key=trials.get)
+        runner.set_tile_shape(*best[0])
+        runner.set_staging(best[1])
+    runner.step(args.warmup)         # warm-up with the chosen variant
+    torch.cuda.synchronize()
+    tshape = runner.tile_shape()
+    staged = runner.staging()[0]
 
     replicas.barrier(ws)
     torch.cuda.synchronize()
@@ -207,88 +324,112 @@ def ours_arm(args):
     tot = []
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
-            flush.zero_()
-            k, total = sim.profile_step(1)
+            if flush is not None:
+                flush.zero_()
+            k, total = runner.profile_step(1)
             for key in kern:
                 kern[key].append(k[key])
             tot.append(total)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    sim.sync()
+    if batch:
+        runner.sync()
+    else:
+        runner.sync()
     replicas.barrier(ws)
     my_ms = replicas.max_over_ranks(float(sum(tot)), ws)
     value = replicas.whole_job_rate(N * args.steps, ws, my_ms * 1e-3) / 1e6
+    if batch:
+        runner.close()
+    nbytes = n_fluid = n_liq = 0
+    for s in sims:
+        b_, f_, l_ = algorithmic_bytes(s.read(pslbm.F_TYPE)["type"], ns, fs, gs)
+        nbytes, n_fluid, n_liq = nbytes + b_, n_fluid + f_, n_liq + l_
+    for s in sims:
+        s.close()
+    del sims, runner
     bulk_ms = statistics.mean(kern["bulk"])
-    bytes_per_launch = n_fluid * 36 * fs + n_liq * 10 * ns * gs + 2 * N
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = bytes_per_launch / (bulk_ms * 1e-3) / 1e9
-    tshape = sim.tile_shape()
-    staged = sim.staging()[0]
+    achieved = nbytes / (bulk_ms * 1e-3) / 1e9
     variant = f"{tshape[0]}x{tshape[1]} {STAGING_NAMES[staged]}"
-    traffic = None
-    if os.path.exists(PROFILE_JSON) and prec == pslbm.FP32:
-        # DRAM bytes per launch from an ncu capture of the same kernel variant
-        # built from the same sources (null otherwise)
-        pj = json.load(open(PROFILE_JSON))
-        if pj.get("source_hash") == profile_case.kernel_source_hash():
-            traffic = pj.get("traffic_per_launch", {}).get(variant)
+    traffic = profile_traffic(args.workload, variant) if prec == pslbm.FP32 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": KERNEL_NAMES[staged], "bytes_per_launch": bytes_per_launch,
-                "kernel_ms": bulk_ms, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "traffic": traffic, "kernel": KERNEL_NAMES[staged], "variant": variant,
+                "bytes_per_launch": nbytes, "kernel_ms": bulk_ms,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
+                else "fallback 6.8 TB/s",
                 "kernel_share": bulk_ms / statistics.mean(tot)}
 
+    cfg = {"workload": WORKLOAD_NAMES[args.workload], "members": len(scenes), "nodes": N,
+           "fluid_nodes": n_fluid, "liquid_nodes": n_liq, "precision": args.precision,
+           "l2": ("flushed (256 MiB write) before every timed step" if flush is not None else
+                  "not flushed: the state is far larger than the 129 MB L2"),
+           "parallelism": f"{'instances sharded over' if batch else 'replicas on'} {ws} GPU(s), no data-path exchange",
+           "tile": f"{tshape[0]}x{tshape[1]}", "staging": STAGING_NAMES[staged],
+           "variant_choice": ("the library's autotuner (each open variant timed for 3 steps)" if trials is None else
+                              "each variant timed for 5 steps under the timed loop's conditions: " +
+                              ", ".join(f"{k[0][0]}x{k[0][1]} {STAGING_NAMES[k[1]]} {v:.4f} ms"
+                                        for k, v in sorted(trials.items())))}
     line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": my_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "fp32", "fp64": "f64", "fp32_f16": "fp32 (f16 solute storage)",
                       "fp32_bf16": "fp32 (bf16 solute storage)"}[args.precision],
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "nx": WORKLOAD["nx"], "ny": WORKLOAD["ny"],
-                       "fluid_nodes": n_fluid, "liquid_nodes": n_liq, "precision": args.precision,
-                       "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
-                       "tile": f"{tshape[0]}x{tshape[1]}", "staging": STAGING_NAMES[staged],
-                       "variant_trials_ms": {f"{k[0][0]}x{k[0][1]} {STAGING_NAMES[k[1]]}": v
-                                             for k, v in sorted(trials.items())}},
-            "roofline": roofline,
+            "data": "synthetic", "config": cfg, "roofline": roofline,
             "kernel_ms": {k: statistics.mean(v) for k, v in kern.items()},
             "gpu_launches": 3 * args.steps}
     if clk:
         line["clocks"] = clk
 
     if not args.skip_cpu:
-        # end to end through the C ABI with host buffers: create (host->device
-        # copy of the scene), then every step a step call and a read of that
-        # step's budget to the host, then a read of all fields
+        # end to end through the public API with host buffers: create every
+        # member from its host arrays (host->device copy of the scenes), then
+        # every step a step call and a read of that step's result (the step
+        # count and status of every member) to the host, then each member's
+        # budget (6 + ns doubles) read back after the last step
         replicas.barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim2 = pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
-                                precision=prec)
+        sims2 = make_sims()
+        if batch:
+            r2 = pslbm.Batch(sims2, tile_x=tshape[0], tile_y=tshape[1])
+            r2.set_staging(staged)
+        else:
+            r2 = sims2[0]
+            r2.set_tile_shape(*tshape[:2])
+            r2.set_staging(staged)
         mon_bytes = 0
         for _ in range(args.steps):
-            sim2.step(1)
-            sim2.monitor()              # the step's result: step count, max rho_1, status
-            mon_bytes += 64
-        out = sim2.read(pslbm.F_RHO1 | pslbm.F_RHO2 | pslbm.F_UX | pslbm.F_UY | pslbm.F_CONC | pslbm.F_TYPE |
-                        pslbm.F_VOL | pslbm.F_BUDGET)
+            r2.step(1)
+            r2.monitor()
+            mon_bytes += 16 * len(sims2) if batch else 64
+        if batch:
+            r2.close()
+        # every member's budget into one device buffer (no allocation per
+        # member), then one copy to the host
+        nb = 6 + ns
+        bud = torch.empty((len(sims2), nb), dtype=torch.float64, device="cuda")
+        for i, s in enumerate(sims2):
+            s.budget_device_noalloc(bud[i].data_ptr())
+        with torch.cuda.stream(stream):
+            budgets = bud.cpu()
+        out_bytes = budgets.numel() * 8
         el = time.perf_counter() - t0
-        sim2.close()
-        h2d = sc["mask"].nbytes + sc["rho1"].nbytes + sc["rho2"].nbytes + sc["conc"].nbytes
-        d2h = sum(v.nbytes for v in out.values()) + mon_bytes
+        for s in sims2:
+            s.close()
+        h2d = sum(sc["mask"].nbytes + sc["rho1"].nbytes + sc["rho2"].nbytes + sc["conc"].nbytes for sc in scenes)
         e2e_val = replicas.whole_job_rate(N * args.steps, ws, replicas.max_over_ranks(el, ws)) / 1e6
         line["e2e"] = {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
-                       "d2h_bytes_per_step": d2h / args.steps,
-                       "note": "scene copied at create; each step's monitor (step count, max rho_1, status) "
-                               "read to the host; all fields and the budget read after the last step"}
+                       "d2h_bytes_per_step": (mon_bytes + out_bytes) / args.steps,
+                       "note": ("members created from host arrays inside the timed region; each step's monitor "
+                                "(step count and status of every member) read to the host; every member's budget "
+                                "read after the last step")}
         if rank == 0:
-            mlups, n, elc = oracle_run(10.0)
-            line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                                    "sample": sample_desc(n, elc)}
-    sim.close()
+            line["cpu_baseline"] = cpu_baseline(args.workload)
     replicas.finish(ws)
     if rank == 0:
         print(json.dumps(line), flush=True)

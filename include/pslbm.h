@@ -123,6 +123,13 @@ typedef struct {
                                       keep their FP32 digits at a large density ratio) */
     int32_t inlet_axis, outlet_axis; /* 0: inlet nodes feed x + 1 and outlet nodes drain x - 1;
                                       1: they feed y + 1 / drain y - 1 (a free top outlet) */
+    double conc_scale[PSLBM_MAX_SPECIES]; /* 16-bit solute storage only: species k's (shifted)
+                                      populations are stored multiplied by conc_scale[k], rounded
+                                      to the nearest power of two (0 is read as 1), so that a
+                                      trace species far below 1 keeps FP16's digits instead of
+                                      falling below its range; scaling by a power of two is
+                                      exact, so only the stored rounding changes.  Ignored for
+                                      FP64 and FP32 storage.  Must be >= 0 and finite. */
 } pslbm_params;
 
 /* Field selectors for pslbm_read_fields; each selected field has its own
@@ -271,6 +278,17 @@ pslbm_status pslbm_batch_get_tile_shape(pslbm_batch_t b, int32_t* tile_x, int32_
  * member has it. */
 pslbm_status pslbm_batch_set_staging(pslbm_batch_t b, int32_t mode);
 pslbm_status pslbm_batch_get_staging(pslbm_batch_t b, int32_t* staged, int32_t* available);
+/* As pslbm_profile_step for a batch: n >= 1 steps without graph capture, each
+ * kernel timed with CUDA events on the library stream; kernel_ms[3] receives
+ * the mean ms per step of the bulk, VOP and amendment kernels over all
+ * members, total_ms (nullable) the mean ms per step.  Synchronises. */
+pslbm_status pslbm_batch_profile_step(pslbm_batch_t b, int64_t n, double* kernel_ms, double* total_ms);
+/* Per-step monitor of a batch: the smallest step count over the members and
+ * the OR of their device status bits (as in pslbm_monitor), gathered on the
+ * device and read in one copy (16 bytes per member).  Synchronises.  The
+ * status bits are reported, not raised: a member's error is returned by
+ * pslbm_batch_sync or by the member's own calls once the batch is gone. */
+pslbm_status pslbm_batch_monitor(pslbm_batch_t b, int64_t* min_steps, uint32_t* status);
 pslbm_status pslbm_batch_destroy(pslbm_batch_t b);
 
 /* ---------------------------------------------------------------- serving

@@ -32,7 +32,7 @@ __global__ void k_init(DevInst* __restrict__ Ip, const uint8_t* __restrict__ mas
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
         const R ja = a == 0 ? J0 : Ja;
-        st<TG, R>(G + ((long long)k * 5 + a) * N + node, ja * c - ja * rp<R>(P).shift_c[k]);
+        gst<TG, R>(P, k, G + ((long long)k * 5 + a) * N + node, ja * c - ja * rp<R>(P).shift_c[k]);
       }
     }
   }
@@ -106,32 +106,13 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
           potentials<R>(P, a1, a2, nps[a], nq1[a], nq2[a], status);
         }
       }
-      R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
-#pragma unroll
-      for (int a = 1; a < 9; ++a) {
-        R ps = nps[a], q1 = nq1[a], q2 = nq2[a];
-        bool take = nlv[a];
-        if (EX(a) != 0 && EY(a) != 0 && !nlv[a]) {
-          const int ah = EX(a) > 0 ? 1 : 3, av = EY(a) > 0 ? 2 : 4;   // the axis links beside it
-          if (nlv[ah] != nlv[av]) {
-            const int m = nlv[ah] ? ah : av;
-            ps = nps[m];
-            q1 = nq1[m];
-            q2 = nq2[m];
-            take = true;
-          }
-        }
-        const R w = wf<R>(a);
-        // differences from the centre value, in the bulk kernels' operation order
-        const R dp = take ? rsub<R>(ps, psc) : R(0);
-        const R d2 = take ? rsub<R>(q2, p2c) : R(0);
-        const R d1 = take ? rsub<R>(q1, p1c) : R(0);
-        const R vs = nlv[a] ? R(0) : w;
-        stencil_acc<R>(spx, w, dp, EX(a)); stencil_acc<R>(s2x, w, d2, EX(a));
-        stencil_acc<R>(s1x, w, d1, EX(a)); stencil_add<R>(ssx, vs, EX(a));
-        stencil_acc<R>(spy, w, dp, EY(a)); stencil_acc<R>(s2y, w, d2, EY(a));
-        stencil_acc<R>(s1y, w, d1, EY(a)); stencil_add<R>(ssy, vs, EY(a));
-      }
+      nps[0] = psc;
+      nq1[0] = p1c;
+      nq2[0] = p2c;
+      nlv[0] = true;
+      const Stencils<R> S = force_stencils<R>(nps, nq1, nq2, nlv);
+      const R spx = S.psx, spy = S.psy, s2x = S.p2x, s2y = S.p2y, s1x = S.p1x, s1y = S.p1y, ssx = S.ssx,
+              ssy = S.ssy;
       const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0], w2 = rp<R>(P).w_adh[1];
       const R F1x = force1<R>(G11, G12, w1, psc, p1c, spx, s2x, ssx, rho1, rp<R>(P).gx);
       const R F1y = force1<R>(G11, G12, w1, psc, p1c, spy, s2y, ssy, rho1, rp<R>(P).gy);
@@ -153,9 +134,9 @@ __global__ void k_fields(const DevInst* __restrict__ Ip, double* __restrict__ o_
         double c = 0.0;
         if (t == T_LIQUID) {
           const TG* gk = G + (long long)k * 5 * N;
-          R s = ldc<R>(gk + node);
+          R s = gldc<R>(P, k, gk + node);
 #pragma unroll
-          for (int a = 1; a < 5; ++a) s += ldc<R>(gk + a * N + node);
+          for (int a = 1; a < 5; ++a) s += gldc<R>(P, k, gk + a * N + node);
           c = double(rp<R>(P).shift_c[k] + s);
         }
         o_conc[k * N + node] = c;
@@ -196,9 +177,9 @@ __global__ void __launch_bounds__(BUD_THREADS) k_budget_partial(const DevInst* _
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         const TG* gk = G + (long long)k * 5 * N;
-        R s = ldc<R>(gk + node);
+        R s = gldc<R>(P, k, gk + node);
 #pragma unroll
-        for (int a = 1; a < 5; ++a) s += ldc<R>(gk + a * N + node);
+        for (int a = 1; a < 5; ++a) s += gldc<R>(P, k, gk + a * N + node);
         acc[3 + k] += double(rp<R>(P).shift_c[k] + s);
       }
     }

@@ -49,9 +49,9 @@ __device__ __forceinline__ void conc_at(const TG* gin, int N, int node, const De
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     const TG* gk = gin + k * 5 * N;
-    R s = ld<R>(gk + node);
+    R s = gld<R>(P, k, gk + node);
 #pragma unroll
-    for (int a = 1; a < 5; ++a) s += ld<R>(gk + a * N + node);
+    for (int a = 1; a < 5; ++a) s += gld<R>(P, k, gk + a * N + node);
     C[k] = rp<R>(P).shift_c[k] + s;
   }
 }
@@ -219,6 +219,17 @@ __device__ __noinline__ void amend_marking(const DevParams& P, const uint8_t* ti
   for (int k = 0; k < NS; ++k) cb[k] = nsrc ? base[k] / R(nsrc) : R(0);
 }
 
+// Densities of a reservoir node at this step (out of line: only inlet and
+// outlet nodes take this path).
+template <class R, class TF>
+__device__ __noinline__ void res_density(const DevParams& P, uint8_t t, unsigned long long step, const uint8_t* tin,
+                                         const TF* fin, int N, int idx, R theta, R& r1, R& r2) {
+  double a, b;
+  reservoir_rho(P, t, step, t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, idx, theta), a, b);
+  r1 = R(a);
+  r2 = R(b);
+}
+
 // Reservoir node: push its equilibrium state (densities of reservoir_rho,
 // velocity of the node downstream of an inlet / upstream of an outlet) into
 // its fluid neighbours, and the solute equilibrium into its liquid neighbours
@@ -297,7 +308,7 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
           const R eu = R(EX(a)) * ux + R(EY(a)) * uy;   // exact
           const R geq = geq_shifted<R>(Ja, Cr[k], rp<R>(P).shift_c[k], eu);
           nbr(P, x, y, EX(a), EY(a), xn, yn);
-          st<TG, R>(gout + (k * 5 + a) * N + yn * P.nx + xn, geq);
+          gst<TG, R>(P, k, gout + (k * 5 + a) * N + yn * P.nx + xn, geq);
         }
       }
     }
@@ -426,7 +437,16 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   const bool own_fluid = is_fluid(own_t) && own_idx >= 0;
   if (own_fluid) src.own_f(own_idx, f1, f2);
   if constexpr (NS > 0) {
-    if (own && own_t == T_LIQUID) src.own_g(node, gs);
+    if (own && own_t == T_LIQUID) {
+      src.own_g(node, gs);
+      if constexpr (Is16<TG>::value) {
+        // undo the species' storage scale (a power of two: exact)
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+#pragma unroll
+          for (int a = 0; a < 5; ++a) gs[k][a] = gs[k][a] * rp<R>(P).gs_div[k];
+      }
+    }
   }
   R r1r = R(0), r2r = R(0);
   if (tid < SH::RING && is_fluid(ring_t)) {
@@ -438,56 +458,40 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   // prefetch the next tile's node types
   next_types(tt);
 
-  // ---- moments of the own node (Eq. 9), potentials -> shared
+  // ---- moments of the own node (Eq. 9)
   R rho1 = R(0), rho2 = R(0), d1 = R(0), d2 = R(0), j1x = R(0), j1y = R(0), j2x = R(0), j2y = R(0);
-  {
-    R r1 = R(0), r2 = R(0);
-    if (own_fluid) {
-      d1 = f1[0];
-      d2 = f2[0];
+  if (own_fluid) {
+    d1 = f1[0];
+    d2 = f2[0];
 #pragma unroll
-      for (int a = 1; a < 9; ++a) {
-        d1 += f1[a];
-        d2 += f2[a];
-      }
-      j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
-      j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
-      j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
-      j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
-      rho1 = sh1 + d1;
-      rho2 = sh2 + d2;
-      r1 = rho1;
-      r2 = rho2;
-      if (!(rho1 == rho1 && rho2 == rho2)) status |= ST_NONFINITE;
-    } else if (is_res(own_t)) {
-      double a, b;
-      reservoir_rho(P, own_t, step, own_t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, own_idx, theta),
-                    a, b);
-      r1 = R(a);
-      r2 = R(b);
+    for (int a = 1; a < 9; ++a) {
+      d1 += f1[a];
+      d2 += f2[a];
     }
-    R ps = R(0), p1 = R(0), p2 = R(0);
-    if (is_live(own_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
-    const bool mk = is_live(own_t) && r1 > theta;
-    spot[eo] = Pot<R>{ps, p1, p2, code_bits<R>(node_code(own_t, mk))};
-    st_[eo] = own_t;
-    sm_[eo] = mk ? 1 : 0;
+    j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
+    j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
+    j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
+    j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
+    rho1 = sh1 + d1;
+    rho2 = sh2 + d2;
+    if (!(rho1 == rho1 && rho2 == rho2)) status |= ST_NONFINITE;
   }
-  if (tid < SH::RING) {
-    R r1 = r1r, r2 = r2r;
-    if (is_res(ring_t)) {
-      double a, b;
-      reservoir_rho(P, ring_t, step, ring_t == T_OUTLET && outlet_up_liquid<R, TF>(P, tin, fin, N, ring_idx, theta),
-                    a, b);
-      r1 = R(a);
-      r2 = R(b);
-    }
+  // ---- potentials of the own node and (tid < RING) one ring node -> shared.
+  // One loop body, not unrolled, serves both, so the equation of state, the
+  // exponentials and the reservoir path are emitted once.
+#pragma unroll 1
+  for (int w = 0; w < 2; ++w) {
+    if (w == 1 && tid >= SH::RING) break;
+    const uint8_t tw = w ? ring_t : own_t;
+    R r1 = w ? r1r : rho1, r2 = w ? r2r : rho2;
+    if (is_res(tw)) res_density<R, TF>(P, tw, step, tin, fin, N, w ? ring_idx : own_idx, theta, r1, r2);
     R ps = R(0), p1 = R(0), p2 = R(0);
-    if (is_live(ring_t)) potentials<R>(P, r1, r2, ps, p1, p2, status);
-    const bool mk = is_live(ring_t) && r1 > theta;
-    spot[er] = Pot<R>{ps, p1, p2, code_bits<R>(node_code(ring_t, mk))};
-    st_[er] = ring_t;
-    sm_[er] = mk ? 1 : 0;
+    if (is_live(tw)) potentials<R>(P, r1, r2, ps, p1, p2, status);
+    const bool mk = is_live(tw) && r1 > theta;
+    const int slot = w ? er : eo;
+    spot[slot] = Pot<R>{ps, p1, p2, code_bits<R>(node_code(tw, mk))};
+    st_[slot] = tw;
+    sm_[slot] = mk ? 1 : 0;
   }
   if (__syncthreads_or(waited_ok ? 0 : 1)) return true;
   after_sync();
@@ -495,13 +499,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   R mymax = R(-1.0 / 0.0);
   if (own && is_fluid(t)) {
     mymax = rho1;
-    // ---- forces (Eqs. 11, 14a/b, 16) with mirror-image solid neighbours.
-    // The stencils sum w (value(x + e) - value(x)) e, equal to the sums of
-    // Eqs. 11 and 14 since sum_a w e = 0, but free of the cancellation between
-    // nearly equal neighbour values in a bulk phase.  A solid neighbour takes
-    // its mirror image across the wall: the centre itself for an axis link (a
-    // zero difference), and for a diagonal link on a flat wall the live one of
-    // the two axis neighbours beside it (the centre at a corner).
+    // ---- forces (Eqs. 11, 14a/b, 16) with mirror-image solid neighbours
+    // (force_stencils).
     const Pot<R> pc = spot[eo];
     const R psc = pc.ps, p1c = pc.p1, p2c = pc.p2;
     // neighbour codes kept for the pushes: the low nibble of each of the eight
@@ -509,38 +508,26 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
     // axis neighbours (abits, 2 bits per direction)
     unsigned nbits = 0u, abits = 0u;
     const int c0 = code_of<R>(pc.code);
-    R spx = 0, spy = 0, s2x = 0, s2y = 0, s1x = 0, s1y = 0, ssx = 0, ssy = 0;
+    R vps[9], vp1[9], vp2[9];
+    bool lv[9];
+    vps[0] = psc;
+    vp1[0] = p1c;
+    vp2[0] = p2c;
+    lv[0] = true;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
-      const int en = eo + EY(a) * SH::EXT_X + EX(a);
-      const Pot<R> q = spot[en];
+      const Pot<R> q = spot[eo + EY(a) * SH::EXT_X + EX(a)];
       const int ca = code_of<R>(q.code);
       nbits |= unsigned(ca & 0xF) << (4 * (a - 1));
       if (a < 5) abits |= unsigned((ca >> 5) & 0x3) << (2 * (a - 1));
-      const bool lv = (ca & C_LIVE) != 0;
-      const R w = wf<R>(a);
-      R vps = q.ps, vp1 = q.p1, vp2 = q.p2;
-      bool take = lv;
-      if (EX(a) != 0 && EY(a) != 0 && !lv) {
-        const Pot<R> qh = spot[eo + EX(a)];
-        const Pot<R> qv = spot[eo + EY(a) * SH::EXT_X];
-        const bool lh = (code_of<R>(qh.code) & C_LIVE) != 0, lw = (code_of<R>(qv.code) & C_LIVE) != 0;
-        if (lh != lw) {
-          vps = lh ? qh.ps : qv.ps;
-          vp1 = lh ? qh.p1 : qv.p1;
-          vp2 = lh ? qh.p2 : qv.p2;
-          take = true;
-        }
-      }
-      const R dp = take ? rsub<R>(vps, psc) : R(0);
-      const R d2 = take ? rsub<R>(vp2, p2c) : R(0);
-      const R d1 = take ? rsub<R>(vp1, p1c) : R(0);
-      const R vs = lv ? R(0) : w;
-      stencil_acc<R>(spx, w, dp, EX(a)); stencil_acc<R>(s2x, w, d2, EX(a));
-      stencil_acc<R>(s1x, w, d1, EX(a)); stencil_add<R>(ssx, vs, EX(a));
-      stencil_acc<R>(spy, w, dp, EY(a)); stencil_acc<R>(s2y, w, d2, EY(a));
-      stencil_acc<R>(s1y, w, d1, EY(a)); stencil_add<R>(ssy, vs, EY(a));
+      lv[a] = (ca & C_LIVE) != 0;
+      vps[a] = q.ps;
+      vp1[a] = q.p1;
+      vp2[a] = q.p2;
     }
+    const Stencils<R> S = force_stencils<R>(vps, vp1, vp2, lv);
+    const R spx = S.psx, spy = S.psy, s2x = S.p2x, s2y = S.p2y, s1x = S.p1x, s1y = S.p1y, ssx = S.ssx,
+            ssy = S.ssy;
     const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0],
             w2 = rp<R>(P).w_adh[1];
     const R F1x = force1<R>(G11, G12, w1, psc, p1c, spx, s2x, ssx, rho1, rp<R>(P).gx);
@@ -646,13 +633,15 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
       const R dl = shs - rp<R>(P).shift_f[s], dg = shs - rp<R>(P).shift_fg[s];
       const R down = liq ? dl : dg;
       TF* fo = fout + s * 9 * N;
+      // Eq. 8 relative to the node's shift, for opposite directions a, a'
+      // together: w (dr + rho (4.5 (e.u)^2 - 1.5 u^2)) +- 3 w rho e.u
+      R feq[9];
+      feq_pairs<R>(dr, rho, ux, uy, uu, feq);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         const R fa = s == 0 ? f1[a] : f2[a];
-        const R eu = R(EX(a)) * ux + R(EY(a)) * uy;   // exact: e has components 0, +-1
         const R w = w9<R>(a);
-        const R feq = feq_shifted<R>(w, dr, rho, eu, uu);
-        const R fs = bgk<R>(fa, feq, itau, w, Ssrc);
+        const R fs = bgk<R>(fa, feq[a], itau, w, Ssrc);
         if (a == 0) {
           st<TF, R>(fo + node, rfma<R>(w, down, fs));
           continue;
@@ -673,9 +662,14 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
     // ---- solute collision (Eqs. 20-22 with u_r) and push streaming
     if constexpr (NS > 0) {
       if (liq) {
+        // Eq. 21 relative to the species' shift, opposite directions together:
+        // J_a (C - shift) +- C e.u / 2
+        R geq[NS][5];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) geq_pairs<R>(rp<R>(P).J0[k], rp<R>(P).Ja[k], C[k], rp<R>(P).shift_c[k], urx, ury,
+                                                  geq[k]);
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
-          const R eu = R(EX(a)) * urx + R(EY(a)) * ury;
           // the rest population stays; a moving one goes into a liquid
           // neighbour, out into a liquid reservoir, or bounces back here
           // (no-flux / mineral link)
@@ -692,9 +686,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
             const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
-            const R geq = geq_shifted<R>(ja, C[k], rp<R>(P).shift_c[k], eu);
-            const R gst = bgk<R>(gs[k][a], geq, rp<R>(P).inv_tau_g[k], ja, Sk[k]);
-            if (keep) st<TG, R>(gout + (k * 5 + slot) * N + dst, gst);
+            const R gs_ = bgk<R>(gs[k][a], geq[k][a], rp<R>(P).inv_tau_g[k], ja, Sk[k]);
+            if (keep) gst<TG, R>(P, k, gout + (k * 5 + slot) * N + dst, gs_);
           }
         }
       } else {
@@ -703,8 +696,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
         for (int k = 0; k < NS; ++k) {
 #pragma unroll
           for (int a = 0; a < 5; ++a)
-            st<TG, R>(gout + (k * 5 + a) * N + node,
-                      -(a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k]) * rp<R>(P).shift_c[k]);
+            gst<TG, R>(P, k, gout + (k * 5 + a) * N + node,
+                       -(a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k]) * rp<R>(P).shift_c[k]);
         }
       }
     }

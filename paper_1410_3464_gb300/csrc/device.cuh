@@ -77,6 +77,9 @@ struct DevParamsR {
   // reactive link rule (Eqs. 29-31 as a halfway wall): link flux q = out * qa - qc,
   // returning population out - q, out = stored + sh (the stored shift J_a C_0 undone)
   R vB_qa, vB_sh, vF_qa, vF_qc, vF_sh;
+  // 16-bit solute storage: stored value = shifted population * gs_mul[k];
+  // loaded value * gs_div[k] (powers of two, so both are exact)
+  R gs_mul[MAXS], gs_div[MAXS];
 };
 
 struct DevParams {
@@ -101,6 +104,7 @@ struct DevParams {
   unsigned long long seed;
   double rho_in_liq[2], rho_in_gas[2], rho_out[2], rho_out_gas[2];
   double conc_in[MAXS];
+  double gs_scale[MAXS];   // 16-bit solute storage scale per species (a power of two; 1 otherwise)
   DevParamsR<float> rf;
   DevParamsR<double> rd;
 };
@@ -177,10 +181,35 @@ template <> __device__ __forceinline__ void st<__half, float>(__half* p, float v
 template <> __device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
   *p = __float2bfloat16_rn(v);
 }
+// Solute populations in 16-bit storage carry a per-species power-of-two
+// scale (pslbm_params.conc_scale); FP32 and FP64 storage carry none.
+template <class T> struct Is16 { static constexpr bool value = false; };
+template <> struct Is16<__half> { static constexpr bool value = true; };
+template <> struct Is16<__nv_bfloat16> { static constexpr bool value = true; };
+
 // plain (coherent) loads for data written earlier in the same kernel sequence
 template <class R, class T> __device__ __forceinline__ R ldc(const T* p) { return R(to_f<T>(*p)); }
 template <> __device__ __forceinline__ double ldc<double, double>(const double* p) { return *p; }
 template <> __device__ __forceinline__ float ldc<float, float>(const float* p) { return *p; }
+
+// Solute population of species k as the compute precision sees it: the
+// stored value times the species' storage scale (16-bit storage only).
+// gld: read-only path (__ldg); gldc: coherent load; gst: store.
+template <class R, class TG>
+__device__ __forceinline__ R gld(const DevParams& P, int k, const TG* p) {
+  if constexpr (Is16<TG>::value) return ld<R>(p) * rp<R>(P).gs_div[k];
+  else return ld<R>(p);
+}
+template <class R, class TG>
+__device__ __forceinline__ R gldc(const DevParams& P, int k, const TG* p) {
+  if constexpr (Is16<TG>::value) return ldc<R>(p) * rp<R>(P).gs_div[k];
+  else return ldc<R>(p);
+}
+template <class TG, class R>
+__device__ __forceinline__ void gst(const DevParams& P, int k, TG* p, R v) {
+  if constexpr (Is16<TG>::value) st<TG, R>(p, v * rp<R>(P).gs_mul[k]);
+  else st<TG, R>(p, v);
+}
 
 // Neighbour coordinate with periodic wrap; false outside a non-periodic edge.
 __device__ __forceinline__ bool nbr(const DevParams& P, int x, int y, int dx, int dy, int& xn, int& yn) {
@@ -325,7 +354,7 @@ template <class R> __device__ __forceinline__ R psi_arg(const DevParams& P, R rh
   const R poly = rfma<R>(eta, rfma<R>(eta, om, R(1)), R(1));
   const R num = rmul<R>(rmul<R>(rho, Q.eos_RT), poly);
   const R p = rfma<R>(-rmul<R>(Q.eos_a, rho), rho, rdiv<R>(num, rmul<R>(rmul<R>(om, om), om)));
-  return rmul<R>(Q.six_over_G11, rsub<R>(p, rdiv<R>(rho, R(3))));
+  return rmul<R>(Q.six_over_G11, rsub<R>(p, rmul<R>(rho, R(1.0 / 3.0))));
 }
 
 template <class R> __device__ __forceinline__ R rrcp(R v);
@@ -338,18 +367,58 @@ template <class R> __device__ __forceinline__ R rexp(R v);
 template <> __device__ __forceinline__ double rexp<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float rexp<float>(float v) { return expf(v); }
 
-// One term of the force stencils along one axis (dir = +1, -1 or 0, a
-// constant once the direction loop is unrolled): s += dir w d (fused), and the
-// wall-density stencil s += dir v.
+// The interaction stencils of Eqs. 11, 14 and 16 at one node, from the values
+// of psi_1, phi_1, phi_2 at the node (index 0) and its eight neighbours (1-8,
+// Eq. 7 order) and the neighbours' liveness (fluid or reservoir):
+//   S = sum_a w(|e_a|^2) v(x + e_a) e_a  (w = 1/9 axis, 1/36 diagonal)
+// for each field, and the wall-density sums sum_a w s(x + e_a) e_a with s = 1
+// at non-live neighbours.  A non-live (solid or wall) neighbour takes the value
+// of its mirror image across the wall: the node itself for an axis link, and
+// for a diagonal link the live one of the two axis neighbours beside it when
+// exactly one is live (a flat wall), else the node itself (a corner).  Since
+// sum_a w e_a = 0 the sums are formed from differences of opposite neighbours,
+// (v1 - v3)/9 + ((v5 - v7) + (v8 - v6))/36 along x and (v2 - v4)/9 +
+// ((v5 - v7) - (v8 - v6))/36 along y, which are free of cancellation in a bulk
+// phase.  Outputs: ps (x, y), p2 (x, y) for F_12, p1 (x, y) for F_21, walls (x, y).
 template <class R>
-__device__ __forceinline__ void stencil_acc(R& s, R w, R d, int dir) {
-  if (dir > 0) s = rfma<R>(w, d, s);
-  if (dir < 0) s = rfma<R>(-w, d, s);
+struct Stencils {
+  R psx, psy, p2x, p2y, p1x, p1y, ssx, ssy;
+};
+template <class R>
+__device__ __forceinline__ void pair_sums(const R* v, R& sx, R& sy) {
+  const R d13 = rsub<R>(v[1], v[3]), d24 = rsub<R>(v[2], v[4]);
+  const R d57 = rsub<R>(v[5], v[7]), d86 = rsub<R>(v[8], v[6]);
+  sx = rfma<R>(R(1.0 / 9.0), d13, rmul<R>(R(1.0 / 36.0), radd<R>(d57, d86)));
+  sy = rfma<R>(R(1.0 / 9.0), d24, rmul<R>(R(1.0 / 36.0), rsub<R>(d57, d86)));
 }
 template <class R>
-__device__ __forceinline__ void stencil_add(R& s, R v, int dir) {
-  if (dir > 0) s = radd<R>(s, v);
-  if (dir < 0) s = rsub<R>(s, v);
+__device__ __forceinline__ Stencils<R> force_stencils(R (&ps)[9], R (&p1)[9], R (&p2)[9], const bool (&lv)[9]) {
+  int ix = 0, iy = 0;   // wall-density sums in units of 1/36
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    if (a >= 5 && !lv[a]) {
+      // ah, av are constants once the loop is unrolled: selects, no indexing
+      const int ah = EX(a) > 0 ? 1 : 3, av = EY(a) > 0 ? 2 : 4;
+      const bool flat = lv[ah] != lv[av], h = lv[ah];
+      ps[a] = flat ? (h ? ps[ah] : ps[av]) : ps[0];
+      p1[a] = flat ? (h ? p1[ah] : p1[av]) : p1[0];
+      p2[a] = flat ? (h ? p2[ah] : p2[av]) : p2[0];
+    } else if (!lv[a]) {
+      ps[a] = ps[0];
+      p1[a] = p1[0];
+      p2[a] = p2[0];
+    }
+    const int sw = lv[a] ? 0 : (a < 5 ? 4 : 1);
+    ix += EX(a) * sw;
+    iy += EY(a) * sw;
+  }
+  Stencils<R> S;
+  pair_sums<R>(ps, S.psx, S.psy);
+  pair_sums<R>(p2, S.p2x, S.p2y);
+  pair_sums<R>(p1, S.p1x, S.p1y);
+  S.ssx = rmul<R>(R(ix), R(1.0 / 36.0));
+  S.ssy = rmul<R>(R(iy), R(1.0 / 36.0));
+  return S;
 }
 
 // F_1 (Eqs. 11, 14a, 16 and the body force) from its stencil sums, and F_2
@@ -399,6 +468,41 @@ __device__ __forceinline__ R half_u2(R ux, R uy) {
 template <class R>
 __device__ __forceinline__ R geq_shifted(R ja, R C, R sh, R eu) {
   return rfma<R>(ja, rsub<R>(C, sh), rmul<R>(rmul<R>(R(0.5), C), eu));
+}
+
+// The nine D2Q9 equilibria of Eq. 8 relative to a node's shift, dr = rho -
+// shift, uu = 1.5 |u|^2, evaluated for opposite directions together: the part
+// even in e.u, w (dr + rho (4.5 (e.u)^2 - uu)), is shared and the odd part
+// 3 w rho e.u is added and subtracted.
+template <class R>
+__device__ __forceinline__ void feq_pairs(R dr, R rho, R ux, R uy, R uu, R* feq) {
+  const R ws = R(1.0 / 9.0), wd = R(1.0 / 36.0);
+  feq[0] = rmul<R>(R(4.0 / 9.0), rfma<R>(rho, -uu, dr));
+  const R a3s = rmul<R>(R(1.0 / 3.0), rho), a3d = rmul<R>(R(1.0 / 12.0), rho);   // 3 w rho
+  // (1, 3): e.u = ux; (2, 4): uy; (5, 7): ux + uy; (6, 8): uy - ux
+  const R e[4] = {ux, uy, radd<R>(ux, uy), rsub<R>(uy, ux)};
+  constexpr int pa[4] = {1, 2, 5, 6}, pb[4] = {3, 4, 7, 8};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R w = q < 2 ? ws : wd, a3 = q < 2 ? a3s : a3d;
+    const R sym = rmul<R>(w, rfma<R>(rho, rfma<R>(R(4.5), rmul<R>(e[q], e[q]), -uu), dr));
+    const R asym = rmul<R>(a3, e[q]);
+    feq[pa[q]] = radd<R>(sym, asym);
+    feq[pb[q]] = rsub<R>(sym, asym);
+  }
+}
+
+// The five D2Q5 equilibria of Eq. 21 relative to the species' shift sh:
+// J_a (C - sh) + C e.u / 2, opposite directions together.
+template <class R>
+__device__ __forceinline__ void geq_pairs(R J0, R Ja, R C, R sh, R ux, R uy, R* geq) {
+  const R cs = rsub<R>(C, sh), hc = rmul<R>(R(0.5), C);
+  const R sa = rmul<R>(Ja, cs), ax = rmul<R>(hc, ux), ay = rmul<R>(hc, uy);
+  geq[0] = rmul<R>(J0, cs);
+  geq[1] = radd<R>(sa, ax);
+  geq[3] = rsub<R>(sa, ax);
+  geq[2] = radd<R>(sa, ay);
+  geq[4] = rsub<R>(sa, ay);
 }
 
 // exp(v) - 1 without the cancellation of evaluating exp(v) first (phi_1 of

@@ -69,10 +69,10 @@ __device__ __forceinline__ void vop_node(const DevInst* Ip, const DevParams& P, 
       oB[b - 1] = oE[b - 1] = oF[b - 1] = R(0);
       if (nn < 0) continue;
       if (useB) {
-        oB[b - 1] = ldc<R>(gout + (P.iB * 5 + b) * N + nn);
-        if (P.iE >= 0) oE[b - 1] = ldc<R>(gout + (P.iE * 5 + b) * N + nn);
+        oB[b - 1] = gldc<R>(P, P.iB, gout + (P.iB * 5 + b) * N + nn);
+        if (P.iE >= 0) oE[b - 1] = gldc<R>(P, P.iE, gout + (P.iE * 5 + b) * N + nn);
       }
-      if (useF) oF[b - 1] = ldc<R>(gout + (P.iF * 5 + b) * N + nn);
+      if (useF) oF[b - 1] = gldc<R>(P, P.iF, gout + (P.iF * 5 + b) * N + nn);
     }
 #pragma unroll
     for (int b = 1; b < 5; ++b) {
@@ -84,16 +84,16 @@ __device__ __forceinline__ void vop_node(const DevInst* Ip, const DevParams& P, 
         const R out = oB[b - 1] + sh;
         const R q = out * rp<R>(P).vB_qa;
         const R bk = out - q;
-        st<TG, R>(gout + (iB * 5 + b) * N + nn, bk - sh);
+        gst<TG, R>(P, iB, gout + (iB * 5 + b) * N + nn, bk - sh);
         sB += q;
-        if (P.iE >= 0) st<TG, R>(gout + (P.iE * 5 + b) * N + nn, oE[b - 1] + q);
+        if (P.iE >= 0) gst<TG, R>(P, P.iE, gout + (P.iE * 5 + b) * N + nn, oE[b - 1] + q);
       }
       if (useF) {
         const int iF = P.iF;
         const R sh = rp<R>(P).vF_sh;
         const R out = oF[b - 1] + sh;
         const R q = out * rp<R>(P).vF_qa - rp<R>(P).vF_qc;
-        st<TG, R>(gout + (iF * 5 + b) * N + nn, (out - q) - sh);
+        gst<TG, R>(P, iF, gout + (iF * 5 + b) * N + nn, (out - q) - sh);
         sF += q;
       }
     }
@@ -299,9 +299,9 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
           const TG* gk = G + (long long)k * 5 * N;
-          R c = ldc<R>(gk + nn);
+          R c = gldc<R>(P, k, gk + nn);
 #pragma unroll
-          for (int a = 1; a < 5; ++a) c += ldc<R>(gk + a * N + nn);
+          for (int a = 1; a < 5; ++a) c += gldc<R>(P, k, gk + a * N + nn);
           sc[k] += rp<R>(P).shift_c[k] + c;
         }
         ++nl;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
         const R ja = a == 0 ? J0 : Ja;
-        st<TG, R>(G + ((long long)k * 5 + a) * N + node, ja * c - ja * rp<R>(P).shift_c[k]);
+        gst<TG, R>(P, k, G + ((long long)k * 5 + a) * N + node, ja * c - ja * rp<R>(P).shift_c[k]);
       }
     }
   }
@@ -363,9 +363,9 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
           const TG* gk = G + (long long)k * 5 * N;
-          R c = ldc<R>(gk + w);
+          R c = gldc<R>(P, k, gk + w);
 #pragma unroll
-          for (int a = 1; a < 5; ++a) c += ldc<R>(gk + a * N + w);
+          for (int a = 1; a < 5; ++a) c += gldc<R>(P, k, gk + a * N + w);
           addc[k] += (rp<R>(P).shift_c[k] + c) / R(nl);
         }
       }
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ 
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
           TG* p = G + ((long long)k * 5 + a) * N + n;
-          st<TG, R>(p, ldc<R>(p) + (a == 0 ? J0 : Ja) * addc[k]);
+          gst<TG, R>(P, k, p, gldc<R>(P, k, p) + (a == 0 ? J0 : Ja) * addc[k]);
         }
       }
     }

@@ -105,6 +105,8 @@ struct pslbm_batch_s {
   const Launchers* L = nullptr;
   std::string err;
   pslbm_status sticky = PSLBM_OK;
+  unsigned long long* mon = nullptr;       // device: (step, status) per member, for pslbm_batch_monitor
+  std::vector<unsigned long long> mon_h;
 };
 
 namespace {
@@ -176,6 +178,8 @@ std::string validate(const pslbm_params* p) {
     return "k4 must be in [0, (1 - J0_F)/2)";
   if (!(p->V_split > 1.0)) return "V_split must be > 1";
   if (!(p->r1_surface_factor >= 0.0) || !std::isfinite(p->r1_surface_factor)) return "r1_surface_factor must be >= 0";
+  for (int k = 0; k < PSLBM_MAX_SPECIES; ++k)
+    if (!(p->conc_scale[k] >= 0.0) || !std::isfinite(p->conc_scale[k])) return "conc_scale must be >= 0 and finite";
   if (p->inlet_axis < 0 || p->inlet_axis > 1 || p->outlet_axis < 0 || p->outlet_axis > 1) return "axes must be 0 or 1";
   if (p->inlet_period_liq < 0 || p->inlet_period_gas < 0 ||
       (p->inlet_period_gas > 0 && p->inlet_period_liq + p->inlet_period_gas <= 0))
@@ -216,6 +220,8 @@ void fill_r(DevParamsR<R>& q, const DevParams& P) {
     q.conc_in[k] = R(P.conc_in[k]);
     q.cR1[k] = R(P.cR1[k]);
     q.cR3[k] = R(P.cR3[k]);
+    q.gs_mul[k] = R(P.gs_scale[k]);
+    q.gs_div[k] = R(1.0 / P.gs_scale[k]);
   }
   q.k1 = R(P.k1);
   q.k1_inv_Keq = R(P.k1 * P.inv_Keq);
@@ -290,6 +296,14 @@ DevParams to_dev(const pslbm_params* p) {
     P.tau_g[k] = k < p->n_species ? p->tau_g[k] : 1.0;
     P.shift_c[k] = p->precision == PSLBM_FP64 ? 0.0 : p->conc_ref[k];
     P.conc_in[k] = p->conc_in[k];
+    // nearest power of two of conc_scale (0: 1), for 16-bit storage only
+    double sc = 1.0;
+    if (p->precision >= PSLBM_FP32_SOLUTE_F16 && p->conc_scale[k] > 0.0) {
+      int e = (int)std::lround(std::log2(p->conc_scale[k]));
+      e = std::max(-60, std::min(60, e));
+      sc = std::ldexp(1.0, e);
+    }
+    P.gs_scale[k] = sc;
   }
   for (int s = 0; s < 2; ++s) P.inv_tau[s] = 1.0 / p->tau[s];
   for (int k = 0; k < MAXS; ++k) {
@@ -372,17 +386,79 @@ void free_all(pslbm_t h) {
   h->allocs.clear();
 }
 
+// Enqueue one launch of the bulk kernel of a variant.
+void enqueue_bulk(cudaStream_t s, const Stepper& st, int shape, int staged) {
+  if (staged == 2)
+    st.L->bulk_tma1[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
+  else if (staged == 1)
+    st.L->bulk_tma[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
+  else
+    st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single != nullptr);
+}
+
 // Enqueue n steps of the kernels for one bulk-kernel variant.
 void enqueue_steps(cudaStream_t s, const Stepper& st, int shape, int staged, int64_t n) {
   for (int64_t i = 0; i < n; ++i) {
-    if (staged == 2)
-      st.L->bulk_tma1[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
-    else if (staged == 1)
-      st.L->bulk_tma[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single);
-    else
-      st.L->bulk[shape](s, st.tiles[shape], st.ntiles[shape], st.d, st.single != nullptr);
+    enqueue_bulk(s, st, shape, staged);
     st.L->vop(s, st.d, st.chunk_map, st.nchunks);
     st.L->amend(s, st.ninst, st.d);
+  }
+}
+
+// n steps without graph capture, each kernel bracketed by CUDA events on the
+// library stream: mean ms per step of the bulk, VOP and amendment kernels and
+// of the whole step.
+pslbm_status profile_steps(Stepper& st, int64_t n, double* kernel_ms, double* total_ms, std::string& err) {
+  cudaStream_t s = lib_stream();
+  cudaError_t te = ensure_tiles(st, st.shape);
+  if (te != cudaSuccess) {
+    err = std::string("tile list: ") + cudaGetErrorString(te);
+    return PSLBM_ERR_CUDA;
+  }
+  cudaEvent_t ev[4] = {};
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+      err = "cudaEventCreate failed";
+      return PSLBM_ERR_CUDA;
+    }
+  double acc[3] = {0, 0, 0}, tot = 0;
+  pslbm_status st_ = PSLBM_OK;
+  for (int64_t i = 0; i < n; ++i) {
+    cudaEventRecord(ev[0], s);
+    enqueue_bulk(s, st, st.shape, st.staged);
+    cudaEventRecord(ev[1], s);
+    st.L->vop(s, st.d, st.chunk_map, st.nchunks);
+    cudaEventRecord(ev[2], s);
+    st.L->amend(s, st.ninst, st.d);
+    cudaEventRecord(ev[3], s);
+    cudaError_t e = cudaEventSynchronize(ev[3]);
+    if (e != cudaSuccess) {
+      err = std::string("profile step: ") + cudaGetErrorString(e);
+      st_ = PSLBM_ERR_CUDA;
+      break;
+    }
+    float ms;
+    for (int k = 0; k < 3; ++k) {
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+    cudaEventElapsedTime(&ms, ev[0], ev[3]);
+    tot += ms;
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (st_ != PSLBM_OK) return st_;
+  for (int k = 0; k < 3; ++k) kernel_ms[k] = acc[k] / double(n);
+  if (total_ms) *total_ms = tot / double(n);
+  return PSLBM_OK;
+}
+
+// Step count and status bits of every member of a batch, gathered into one
+// device buffer (out[2 i], out[2 i + 1]) for a single copy to the host.
+__global__ void k_batch_monitor(const DevInst* __restrict__ insts, int n, unsigned long long* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    out[2 * i] = insts[i].scal[S_STEP];
+    out[2 * i + 1] = insts[i].scal[S_STATUS];
   }
 }
 
@@ -808,46 +884,9 @@ pslbm_status pslbm_profile_step(pslbm_t h, int64_t n, double* kernel_ms, double*
   if (h->sticky) return h->sticky;
   if (n < 1 || !kernel_ms) return fail(h, PSLBM_ERR_PARAM, "n < 1 or kernel_ms is NULL");
   if (h->in_batch) return fail(h, PSLBM_ERR_STATE, "handle is a member of a batch");
-  cudaStream_t s = lib_stream();
-  {
-    cudaError_t te = ensure_tiles(h->run, h->run.shape);
-    if (te != cudaSuccess) return fail(h, PSLBM_ERR_CUDA, std::string("tile list: ") + cudaGetErrorString(te));
-  }
-  cudaEvent_t ev[4];
-  for (int i = 0; i < 4; ++i) CK(h, cudaEventCreate(&ev[i]));
-  double acc[3] = {0, 0, 0}, tot = 0;
-  pslbm_status st = PSLBM_OK;
-  for (int64_t i = 0; i < n && st == PSLBM_OK; ++i) {
-    const int sh = h->run.shape;
-    cudaEventRecord(ev[0], s);
-    if (h->run.staged == 2)
-      h->L->bulk_tma1[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, &h->h.P);
-    else if (h->run.staged == 1)
-      h->L->bulk_tma[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, &h->h.P);
-    else
-      h->L->bulk[sh](s, h->run.tiles[sh], h->run.ntiles[sh], h->d, true);
-    cudaEventRecord(ev[1], s);
-    h->L->vop(s, h->d, nullptr, h->run.nchunks);
-    cudaEventRecord(ev[2], s);
-    h->L->amend(s, 1, h->d);
-    cudaEventRecord(ev[3], s);
-    cudaError_t e = cudaEventSynchronize(ev[3]);
-    if (e != cudaSuccess) {
-      st = fail(h, PSLBM_ERR_CUDA, std::string("profile step: ") + cudaGetErrorString(e));
-      break;
-    }
-    float ms;
-    for (int k = 0; k < 3; ++k) {
-      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-      acc[k] += ms;
-    }
-    cudaEventElapsedTime(&ms, ev[0], ev[3]);
-    tot += ms;
-  }
-  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
-  if (st != PSLBM_OK) return st;
-  for (int k = 0; k < 3; ++k) kernel_ms[k] = acc[k] / double(n);
-  if (total_ms) *total_ms = tot / double(n);
+  std::string err;
+  pslbm_status st = profile_steps(h->run, n, kernel_ms, total_ms, err);
+  if (st != PSLBM_OK) return fail(h, st, err);
   return device_status(h);
 }
 
@@ -1146,11 +1185,57 @@ pslbm_status pslbm_batch_sync(pslbm_batch_t b) {
   return PSLBM_OK;
 }
 
+pslbm_status pslbm_batch_profile_step(pslbm_batch_t b, int64_t n, double* kernel_ms, double* total_ms) {
+  if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
+  if (b->sticky) return b->sticky;
+  if (n < 1 || !kernel_ms) return fail(nullptr, PSLBM_ERR_PARAM, "n < 1 or kernel_ms is NULL");
+  std::string err;
+  pslbm_status st = profile_steps(b->run, n, kernel_ms, total_ms, err);
+  if (st != PSLBM_OK) {
+    b->sticky = st;
+    b->err = err;
+    return fail(nullptr, st, err);
+  }
+  return PSLBM_OK;
+}
+
+pslbm_status pslbm_batch_monitor(pslbm_batch_t b, int64_t* min_steps, uint32_t* status) {
+  if (!b) return fail(nullptr, PSLBM_ERR_PARAM, "batch is NULL");
+  if (b->sticky) return b->sticky;
+  const int n = (int)b->members.size();
+  cudaStream_t s = lib_stream();
+  if (!b->mon) {
+    cudaError_t e = cudaMalloc(&b->mon, (size_t)n * 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->mon = nullptr;
+      return fail(nullptr, PSLBM_ERR_OOM, "batch monitor buffer");
+    }
+    b->mon_h.assign((size_t)n * 2, 0ULL);
+  }
+  k_batch_monitor<<<(n + 255) / 256, 256, 0, s>>>(b->d, n, b->mon);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->mon_h.data(), b->mon, (size_t)n * 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(nullptr, PSLBM_ERR_CUDA, std::string("batch monitor: ") + cudaGetErrorString(e));
+  unsigned long long lo = ~0ULL, bits = 0;
+  for (int i = 0; i < n; ++i) {
+    lo = std::min(lo, b->mon_h[2 * i]);
+    bits |= b->mon_h[2 * i + 1];
+  }
+  if (min_steps) *min_steps = (int64_t)lo;
+  if (status) *status = (uint32_t)bits;
+  return PSLBM_OK;
+}
+
 pslbm_status pslbm_batch_destroy(pslbm_batch_t b) {
   if (!b) return PSLBM_OK;
   cudaStreamSynchronize(lib_stream());
   b->run.release();
   if (b->d) cudaFree(b->d);
+  if (b->mon) cudaFree(b->mon);
   for (pslbm_t m : b->members) m->in_batch = 0;
   delete b;
   return PSLBM_OK;

@@ -8,12 +8,19 @@ what ncu measured on it.
         --steps single steps.  The working set (about 150 MB) is larger than
         the 129 MB L2, so DRAM counters mean something, and small enough for a
         multi-pass ncu capture.
-    python -m paper_1410_3464_gb300.profile_case summarize LAUNCHES.csv OUT.json
+    python -m paper_1410_3464_gb300.profile_case run --batch 32 [--warm 2] [--steps 3] [--only SHAPE:STAGING]
+        the same for a batch of 32 members of the 256-member benchmark trace
+        (every 8th request: sides 128-1024, about 6 M nodes, 1.8 GB of device
+        state): small enough for a multi-pass ncu capture, large enough that
+        DRAM counters mean something.  Its DRAM bytes per launch scale to the
+        256-member batch by the ratio of the algorithmic bytes.
+    python -m paper_1410_3464_gb300.profile_case summarize LAUNCHES.csv OUT.json [--batch 32]
         reads the ncu --csv --print-units base launch list of the run above
         (kernels matching k_bulk, metrics dram__bytes_read.sum,
         dram__bytes_write.sum, gpu__time_duration.sum) and writes, per variant,
         the mean DRAM bytes and duration of the launches after the warm-up,
-        keyed by the hash of the device sources they were built from.
+        keyed by the hash of the device sources they were built from; for a
+        batch also the traffic scaled to the full 256-member batch.
 """
 from __future__ import annotations
 
@@ -55,7 +62,46 @@ def variants(only=None):
     return out
 
 
+def batch_members(count):
+    """Every (256 / count)-th request of the 256-member benchmark trace (seed 4)."""
+    from . import inputs
+    reqs = inputs.request_stream(256, seed=4, size_range=(128, 1024), budget_range=(1000, 10000),
+                                 rate_range=(1e-6, 1e-1), porosity_range=(0.4, 0.8), stop_fraction=0.0)
+    return reqs[::max(1, 256 // count)][:count], reqs
+
+
+def algorithmic_bytes(types, ns):
+    """FP32 bulk-kernel bytes of one step (fluid x 144 + liquid x 40 ns + 2 per node)."""
+    return int((types <= 1).sum()) * 144 + int((types == 0).sum()) * 40 * ns + 2 * types.size
+
+
+def run_batch(args):
+    from . import inputs, pslbm
+    members, _ = batch_members(args.batch)
+    scenes = [inputs.request_scene(r) for r in members]
+    sims = [pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                             precision=pslbm.FP32) for sc in scenes]
+    for shape, g in variants(args.only):
+        b = pslbm.Batch(sims, tile_x=shape[0], tile_y=shape[1])
+        if g and not b.staging()[1]:
+            raise SystemExit("TMA staging unavailable for this batch")
+        b.set_staging(g)
+        for _ in range(args.warm + args.steps):
+            b.step(1)
+        b.sync()
+        b.close()
+        print(f"{variant_name(shape, g)}: {args.warm} + {args.steps} bulk launches", flush=True)
+    alg = sum(algorithmic_bytes(s.read(pslbm.F_TYPE)["type"], s.ns) for s in sims)
+    print(json.dumps({"algorithmic_bytes_per_launch": alg, "members": len(sims),
+                      "nodes": sum(s.nx * s.ny for s in sims)}), flush=True)
+    for s in sims:
+        s.close()
+    return 0
+
+
 def run(args):
+    if args.batch:
+        return run_batch(args)
     from . import inputs, pslbm
     sc = inputs.porous_discs(nx=1024, ny=512, seed=1)
     with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
@@ -99,8 +145,11 @@ def summarize(args):
     per = args.warm + args.steps
     if len(bulk) != per * len(vs):
         raise SystemExit(f"expected {per * len(vs)} bulk launches, found {len(bulk)}")
-    out = {"kernel": "k_bulk (plain loads) / k_bulk_tma (TMA-staged), FP32 storage, 3 species, single simulation",
-           "workload": WORKLOAD, "source_hash": kernel_source_hash(),
+    out = {"kernel": ("k_bulk (plain loads) / k_bulk_tma (TMA-staged), FP32 storage, 3 species, " +
+                      ("batch" if args.batch else "single simulation")),
+           "workload": (f"{args.batch} members of the 256-member benchmark batch (every {256 // args.batch}th "
+                        "request), FP32, 3 species" if args.batch else WORKLOAD),
+           "source_hash": kernel_source_hash(),
            "traffic_per_launch": {}, "dram_bytes_read": {}, "dram_bytes_write": {}, "ncu_duration_us": {},
            "note": ("ncu replays each launch with caches flushed; dram bytes are per launch, means over the "
                     f"{args.steps} launches after {args.warm} warm-up launches of each variant; writes still "
@@ -120,6 +169,16 @@ def summarize(args):
         out["dram_bytes_read"][key] = int(round(rd))
         out["dram_bytes_write"][key] = int(round(wr))
         out["ncu_duration_us"][key] = round(du * 1e6, 2)
+    if args.batch:
+        # scale the small batch's DRAM bytes to the full 256-member batch by the
+        # ratio of the algorithmic bytes (the kernel's traffic per node does not
+        # depend on which members are in the batch)
+        alg_small, alg_full = args.alg_small, args.alg_full
+        out["algorithmic_bytes_small"] = alg_small
+        out["algorithmic_bytes_full"] = alg_full
+        out["traffic_measured_small"] = dict(out["traffic_per_launch"])
+        out["traffic_per_launch"] = {k: int(round(v * alg_full / alg_small))
+                                     for k, v in out["traffic_measured_small"].items()}
     with open(args.out, "w") as fh:
         json.dump(out, fh, indent=1)
         fh.write("\n")
@@ -135,7 +194,10 @@ def main(argv=None):
         p.add_argument("--warm", type=int, default=2)
         p.add_argument("--steps", type=int, default=3)
         p.add_argument("--only", default=None, help="one variant, e.g. 32x8:1")
+        p.add_argument("--batch", type=int, default=0, help="members of the benchmark batch (0: one lattice)")
         if name == "summarize":
+            p.add_argument("--alg-small", type=int, default=0, help="algorithmic bytes per launch of the run")
+            p.add_argument("--alg-full", type=int, default=0, help="algorithmic bytes per launch of the full batch")
             p.add_argument("csv")
             p.add_argument("out")
             p.add_argument("--command", default="", help="the ncu command line that made the csv")

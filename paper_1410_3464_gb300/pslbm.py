@@ -31,7 +31,7 @@ EXPORTS = ["pslbm_get_stream", "pslbm_set_stream", "pslbm_create", "pslbm_step",
            "pslbm_server_fetch", "pslbm_server_release", "pslbm_server_last_error", "pslbm_server_destroy",
            "pslbm_set_tile_shape", "pslbm_get_tile_shape", "pslbm_batch_get_tile_shape",
            "pslbm_set_staging", "pslbm_get_staging", "pslbm_batch_set_staging", "pslbm_batch_get_staging",
-           "pslbm_monitor"]
+           "pslbm_monitor", "pslbm_batch_profile_step", "pslbm_batch_monitor"]
 
 _D2 = C.c_double * 2
 _DS = C.c_double * MAX_SPECIES
@@ -56,7 +56,7 @@ class Params(C.Structure):
         ("rho_in_liq", _D2), ("rho_in_gas", _D2), ("rho_out", _D2), ("rho_out_gas", _D2),
         ("inlet_period_liq", C.c_int32), ("inlet_period_gas", C.c_int32), ("inlet_ramp", C.c_int32),
         ("conc_in", _DS), ("r1_surface_factor", C.c_double), ("rho_ref_gas", _D2),
-        ("inlet_axis", C.c_int32), ("outlet_axis", C.c_int32),
+        ("inlet_axis", C.c_int32), ("outlet_axis", C.c_int32), ("conc_scale", _DS),
     ]
 
 
@@ -145,6 +145,8 @@ def load():
     lib.pslbm_get_staging.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     lib.pslbm_batch_set_staging.argtypes = [vp, i32]
     lib.pslbm_batch_get_staging.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    lib.pslbm_batch_profile_step.argtypes = [vp, i64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.pslbm_batch_monitor.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("pslbm_get_stream", "pslbm_last_error", "pslbm_server_last_error"):
@@ -325,6 +327,20 @@ class Batch:
         sg, av = C.c_int32(), C.c_int32()
         _check(load().pslbm_batch_get_staging(self.b, C.byref(sg), C.byref(av)))
         return sg.value, bool(av.value)
+
+    def profile_step(self, n=1):
+        """Run n steps with per-kernel CUDA-event timing; returns
+        ({'bulk', 'vop', 'amend'} mean ms per step, mean total ms per step)."""
+        k = (C.c_double * 3)()
+        t = C.c_double()
+        _check(load().pslbm_batch_profile_step(self.b, int(n), k, C.byref(t)))
+        return dict(bulk=k[0], vop=k[1], amend=k[2]), t.value
+
+    def monitor(self):
+        """(smallest step count over the members, OR of their status bits)."""
+        n, st = C.c_int64(), C.c_uint32()
+        _check(load().pslbm_batch_monitor(self.b, C.byref(n), C.byref(st)))
+        return n.value, st.value
 
     def close(self):
         if getattr(self, "b", None):

@@ -241,6 +241,31 @@ def test_r1_surface_enhancement(pslbm):
     compare(got, ref, what="R1 surface enhancement")
 
 
+@pytest.mark.parametrize("k1,surface", [(2e-3, 1.0), (2e-5, 100.0)])
+def test_reversible_r1(pslbm, k1, surface):
+    """Eq. 5a with the back reaction: R1 = k1 (C_A - C_B sqrt(C_C) / K_eq), with
+    C_C = rho_2 / M_C taken from the gas component, on the plain scene (the
+    bubble supplies C(g); R1 also turns liquid mass into gas, Eq. 27), without
+    and with the Section 2 surface enhancement (100 times faster at the grain:
+    2e-3 there); 100 steps, FP64 path against the oracle at 1e-12.  B starts at 0.3, so the back reaction is active from the
+    first step, and at the bubble, where C_C is large, R1 runs backwards."""
+    sc = inputs.bubble_grain()
+    p = dict(sc["params"])
+    p.update(k1=k1, inv_Keq=40.0, inv_M_C=1.0 / (0.1 * 0.35813), gas_yield=0.05 * 0.35813,
+             r1_surface_factor=surface, k2=0.0)
+    sc["params"] = p
+    sc["conc"] = sc["conc"].copy()
+    sc["conc"][1] = 0.3
+    got, ref, L = run_both(pslbm, sc, 100)
+    compare(got, ref, what=f"reversible R1 (surface x{surface:g})")
+    # the back reaction is not negligible here: somewhere in the liquid the
+    # oracle's back rate is at least half the forward rate
+    liquid = ref["type"] == 0
+    CC = np.maximum(ref["rho2"] * p["inv_M_C"], 0.0)
+    back = ref["conc"][1] * np.sqrt(CC) * p["inv_Keq"]
+    assert np.max(back[liquid] / ref["conc"][0][liquid]) > 0.5
+
+
 def test_beaker_scene_free_top_outlet(pslbm):
     """The paper's beaker (Section 5): D(s) cylinder r = 15 at (50, 50) in
     100x160, walls left, right and bottom, a free outlet on the top row (outlet
