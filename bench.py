@@ -55,9 +55,9 @@ WORKLOAD_NAMES = {
 }
 # oracle sample: members of the same trace with both sides at most this long
 SAMPLE_SIDE = 256
-STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma 1-stage"}
+STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma d2q9-box"}
 PROFILE_TAGS = {"batch": "batch256", "porous": "porous1024x512", "large": "porous4096x2048"}
-KERNEL_NAMES = {0: "k_bulk", 1: "k_bulk_tma<2 stages>", 2: "k_bulk_tma<1 stage>"}
+KERNEL_NAMES = {0: "k_bulk", 1: "k_bulk_tma<D2Q9+D2Q5 boxes>", 2: "k_bulk_tma<D2Q9 box, 3 blocks>"}
 
 
 def parse():

@@ -206,9 +206,11 @@ pslbm_status pslbm_set_tile_shape(pslbm_t h, int32_t tile_x, int32_t tile_y);
 pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, int32_t* tuned);
 
 /* Staging of the bulk kernel's populations: 0 plain per-thread loads; 1 TMA
- * copies of each tile's population box into shared memory two tiles ahead
- * (two stages, two blocks per SM); 2 the same one tile ahead (one stage, three
- * blocks per SM).  1 and 2 are available for the FP32-population precisions
+ * copies of each tile's D2Q9 and D2Q5 population boxes into shared memory two
+ * tiles ahead (two stages, two blocks per SM); 2 TMA copies of the D2Q9 box
+ * only, one tile ahead, re-read from shared memory where used, with the
+ * solute populations loaded directly (two stages, three blocks per SM).  1 and
+ * 2 are available for the FP32-population precisions
  * when a row of the lattice is a multiple of 16 bytes (nx a multiple of 4, and
  * of 8 with 16-bit solutes).  -1 (the default) leaves the choice to timing.
  * PSLBM_ERR_PARAM for 1 or 2 where they are not available.  The results are bit-identical either way.  get reports the

@@ -364,6 +364,7 @@ __device__ __forceinline__ int next_live(const Tile* tiles, int ntiles, const De
 // stored density sums of a ring node.
 template <class TF, class TG, class R, int NS>
 struct GlobalSrc {
+  static constexpr bool kReread = false;
   const TF* fin;
   const TG* gin;
   int N;
@@ -436,18 +437,22 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   R gs[NS > 0 ? NS : 1][5];
   const bool own_fluid = is_fluid(own_t) && own_idx >= 0;
   if (own_fluid) src.own_f(own_idx, f1, f2);
-  if constexpr (NS > 0) {
-    if (own && own_t == T_LIQUID) {
-      src.own_g(node, gs);
-      if constexpr (Is16<TG>::value) {
-        // undo the species' storage scale (a power of two: exact)
+  // solute populations of a liquid node (undoing the species' storage scale,
+  // a power of two: exact); a re-reading source loads them where used
+  auto load_g = [&] {
+    if constexpr (NS > 0) {
+      if (own && own_t == T_LIQUID) {
+        src.own_g(node, gs);
+        if constexpr (Is16<TG>::value) {
 #pragma unroll
-        for (int k = 0; k < NS; ++k)
+          for (int k = 0; k < NS; ++k)
 #pragma unroll
-          for (int a = 0; a < 5; ++a) gs[k][a] = gs[k][a] * rp<R>(P).gs_div[k];
+            for (int a = 0; a < 5; ++a) gs[k][a] = gs[k][a] * rp<R>(P).gs_div[k];
+        }
       }
     }
-  }
+  };
+  if constexpr (!Src::kReread) load_g();
   R r1r = R(0), r2r = R(0);
   if (tid < SH::RING && is_fluid(ring_t)) {
     R d1r, d2r;
@@ -556,6 +561,7 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
     for (int a = 1; a < 9; ++a) nb[a] = inner ? node + EX(a) + EY(a) * nx : nbr_index(P, x, y, EX(a), EY(a));
 
     // ---- solutes: concentration with the Step-2 amendment, sources
+    if constexpr (Src::kReread) load_g();
     R S1 = R(0), S2 = R(0);
     R C[NS > 0 ? NS : 1];
     R Sk[NS > 0 ? NS : 1];
@@ -632,6 +638,11 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
       const R shs = s == 0 ? sh1 : sh2;
       const R dl = shs - rp<R>(P).shift_f[s], dg = shs - rp<R>(P).shift_fg[s];
       const R down = liq ? dl : dg;
+      if constexpr (Src::kReread) {
+        // the stage still holds this tile: read the component's populations
+        // again rather than keeping them in registers across the barrier
+        src.own_fc(own_idx, s, s == 0 ? f1 : f2);
+      }
       TF* fo = fout + s * 9 * N;
       // Eq. 8 relative to the node's shift, for opposite directions a, a'
       // together: w (dr + rho (4.5 (e.u)^2 - 1.5 u^2)) +- 3 w rho e.u
@@ -777,13 +788,14 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
 
 // Shared-memory stage of the staged kernel: the D2Q9 box of a tile (both
 // components, the tile plus a ring of one node in y and four in x, so that
-// the box's x origin stays on a 16-byte boundary) and the D2Q5 box of the
-// tile itself, as the TMA unit writes them (x fastest, then y, then plane).
-template <class SH, class TG, int NS>
+// the box's x origin stays on a 16-byte boundary) and, when STAGE_G, the D2Q5
+// box of the tile itself, as the TMA unit writes them (x fastest, then y,
+// then plane).
+template <class SH, class TG, int NS, bool STAGE_G = true>
 struct StageCfg {
   static constexpr int BX = SH::TX + 2 * STAGE_HALO_X, BY = SH::TY + 2;
   static constexpr int FBYTES = BX * BY * 18 * 4;
-  static constexpr int GBYTES = NS > 0 ? SH::TX * SH::TY * 5 * NS * (int)sizeof(TG) : 0;
+  static constexpr int GBYTES = (NS > 0 && STAGE_G) ? SH::TX * SH::TY * 5 * NS * (int)sizeof(TG) : 0;
   static constexpr int FOFF = 0;
   static constexpr int GOFF = ((FBYTES + 127) / 128) * 128;
   static constexpr int STAGE = GOFF + ((GBYTES + 127) / 128) * 128;
@@ -792,12 +804,16 @@ struct StageCfg {
 
 // Population source of the staged kernel: the tile's own populations and the
 // ring densities come from the shared stage; nodes that lie across a periodic
-// edge (outside the box) are read from global memory.
-template <class SH, class TG, int NS>
+// edge (outside the box) are read from global memory.  Without STAGE_G the
+// solute populations are read from global memory, and the kernel re-reads the
+// D2Q9 populations from the stage where it needs them instead of holding them
+// in registers across the tile's barrier (kReread).
+template <class SH, class TG, int NS, bool STAGE_G = true>
 struct StageSrc {
-  using C = StageCfg<SH, TG, NS>;
+  using C = StageCfg<SH, TG, NS, STAGE_G>;
+  static constexpr bool kReread = !STAGE_G;
   const float* fs;     // stage D2Q9 box
-  const TG* gs_;       // stage D2Q5 box
+  const TG* gs_;       // stage D2Q5 box (STAGE_G) or the solute populations in global memory
   const float* fin;
   int N, nx, ny, x0, y0;
   // A thread position beyond the lattice edge of a partial tile stands for the
@@ -819,12 +835,31 @@ struct StageSrc {
       }
     }
   }
-  __device__ __forceinline__ void own_g(int, float (*g)[5]) const {
-    const int i = threadIdx.x;
+  // one component's populations (as own_f)
+  __device__ __forceinline__ void own_fc(int idx, int comp, float* f) const {
+    const int tx = threadIdx.x % SH::TX, ty = threadIdx.x / SH::TX;
+    if (x0 + tx < nx && y0 + ty < ny) {
+      const float* b = fs + (ty + 1) * C::BX + (tx + STAGE_HALO_X) + comp * 9 * C::BX * C::BY;
 #pragma unroll
-    for (int k = 0; k < NS; ++k)
+      for (int a = 0; a < 9; ++a) f[a] = b[a * C::BX * C::BY];
+    } else {
 #pragma unroll
-      for (int a = 0; a < 5; ++a) g[k][a] = ldc<float>(gs_ + (k * 5 + a) * SH::TX * SH::TY + i);
+      for (int a = 0; a < 9; ++a) f[a] = ld<float>(fin + (comp * 9 + a) * N + idx);
+    }
+  }
+  __device__ __forceinline__ void own_g(int node, float (*g)[5]) const {
+    if constexpr (STAGE_G) {
+      const int i = threadIdx.x;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+#pragma unroll
+        for (int a = 0; a < 5; ++a) g[k][a] = ldc<float>(gs_ + (k * 5 + a) * SH::TX * SH::TY + i);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+#pragma unroll
+        for (int a = 0; a < 5; ++a) g[k][a] = ld<float>(gs_ + (k * 5 + a) * N + node);
+    }
   }
   __device__ __forceinline__ void ring_density(int ring_idx, int rx, int ry, float& d1, float& d2) const {
     if (rx >= 0 && rx < nx && ry >= 0 && ry < ny) {
@@ -846,36 +881,42 @@ struct StageSrc {
 
 // Issue the TMA copies of the tile `d` into a stage (one thread), from the
 // population maps of its step.
-template <class SH, class TG, int NS>
+template <class SH, class TG, int NS, bool STAGE_G>
 __device__ __forceinline__ void stage_issue(const Tile& d, const CUtensorMap* mf, const CUtensorMap* mg,
                                             unsigned char* stage, uint64_t* bar) {
-  using C = StageCfg<SH, TG, NS>;
+  using C = StageCfg<SH, TG, NS, STAGE_G>;
   mbar_arrive_expect_tx(bar, C::TX_BYTES);
   tma_load_3d(stage + C::FOFF, mf, bar, d.x0 - STAGE_HALO_X, d.y0 - 1, 0);
-  if constexpr (NS > 0) tma_load_3d(stage + C::GOFF, mg, bar, d.x0, d.y0, 0);
+  if constexpr (NS > 0 && STAGE_G) tma_load_3d(stage + C::GOFF, mg, bar, d.x0, d.y0, 0);
 }
 
 // Staged bulk kernel (FP32 populations): the TMA unit brings each tile's
 // population box into shared memory ahead of its use, so the populations'
-// DRAM latency overlaps arithmetic instead of stalling it.  A tile reads its
-// stage only before the tile's barrier (into registers), so the stage can be
-// refilled right after it.  STAGES = 2: two stages, the copy of tile j+2 is
-// issued at tile j's barrier (two blocks per SM fit); STAGES = 1: one stage,
-// the copy of tile j+1 is issued at tile j's barrier (half the shared memory,
-// three blocks per SM).  The arithmetic is the plain kernel's, value for
-// value.
-//
-// SINGLE: every tile belongs to the one simulation at insts[0], whose
-// parameter block comes as a kernel argument (read from the constant bank,
-// uniform across the grid); its step view and population maps are read once,
-// tile descriptors are loaded a tile ahead, and the maximum and status are
-// flushed once at the end.  Otherwise each tile's instance supplies its own
-// block, view and maps, and the accumulators are flushed per tile.
-template <class SH, int SHAPE, class TG, int NS, int STAGES, bool SINGLE>
-__global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
+// DRAM latency overlaps arithmetic instead of stalling it.  Two stages in
+// both modes; the arithmetic is the plain kernel's, value for value.
+//   MODE 1: each stage holds the tile's D2Q9 box and its D2Q5 box; a tile
+//     reads its stage only before the tile's barrier (into registers), so the
+//     copy of tile j+2 is issued into tile j's stage right after tile j's
+//     barrier; two blocks per SM fit.
+//   MODE 2: each stage holds the D2Q9 box only; the solute populations are
+//     read from global memory where they are used, and the D2Q9 populations
+//     are read from the stage again for the collision instead of being held
+//     in registers across the barrier, so the kernel fits three blocks per SM
+//     (fewer registers, 70 KB of shared memory).  The stage of tile j is read
+//     until the end of tile j, so the copy of tile j+1 goes into tile j-1's
+//     stage right after tile j's barrier.
+// Smem bytes of the dynamic stages of a mode.
+template <class SH, class TG, int NS, int MODE>
+constexpr int tma_smem() {
+  return 2 * StageCfg<SH, TG, NS, MODE == 1>::STAGE;
+}
+
+template <class SH, int SHAPE, class TG, int NS, int MODE, bool SINGLE>
+__global__ void __launch_bounds__(NTHREADS, MODE == 1 ? 2 : 3)
     k_bulk_tma(const Tile* __restrict__ tiles, int ntiles, const DevInst* __restrict__ insts,
                const __grid_constant__ DevParams Pk) {
-  using C = StageCfg<SH, TG, NS>;
+  constexpr bool SG = MODE == 1;   // solute box staged too
+  using C = StageCfg<SH, TG, NS, SG>;
   using R = float;
   using View = StepView<float, TG, R>;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -899,9 +940,9 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     const CUtensorMap* mg = &Ip->tmg[SHAPE][cur];
     if constexpr (!SINGLE) {
       tensormap_acquire(mf);
-      if constexpr (NS > 0) tensormap_acquire(mg);
+      if constexpr (NS > 0 && SG) tensormap_acquire(mg);
     }
-    stage_issue<SH, TG, NS>(d, mf, mg, stage, bar);
+    stage_issue<SH, TG, NS, SG>(d, mf, mg, stage, bar);
   };
   int ti = live(blockIdx.x);
   int t1 = ti < ntiles ? live(ti + stride) : ntiles;
@@ -915,13 +956,13 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     fence_barrier_init();
     if constexpr (SINGLE) {
       tensormap_acquire(&insts->tmf[SHAPE][V1.cur]);
-      if constexpr (NS > 0) tensormap_acquire(&insts->tmg[SHAPE][V1.cur]);
+      if constexpr (NS > 0 && SG) tensormap_acquire(&insts->tmg[SHAPE][V1.cur]);
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (ti < ntiles) issue(d0, dyn, &bars[0]);
-    if (STAGES == 2 && t1 < ntiles) issue(SINGLE ? d1 : tiles[t1], dyn + C::STAGE, &bars[1]);
+    if (t1 < ntiles) issue(SINGLE ? d1 : tiles[t1], dyn + C::STAGE, &bars[1]);
   }
   TileTypes tt;
   if (ti < ntiles)
@@ -930,7 +971,7 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
   int j = 0;                        // tiles processed by this block
   uint32_t phase = 0;               // parity bit per stage
   while (ti < ntiles) {
-    const int b = STAGES == 2 ? (j & 1) : 0;     // stage of this tile
+    const int b = j & 1;                          // stage of this tile
     const int sb = j & 1;                         // shared buffers of this tile
     const int t2 = t1 < ntiles ? live(t1 + stride) : ntiles;
     const Tile d2 = SINGLE && t2 < ntiles ? tiles[t2] : Tile{};
@@ -941,13 +982,18 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     const View V = SINGLE ? V1 : step_view<float, TG, R>(Ip);
     unsigned char* stage = dyn + b * C::STAGE;
     const DevParams& P = SINGLE ? Pk : Ip->P;
-    const StageSrc<SH, TG, NS> src{(const float*)(stage + C::FOFF), (const TG*)(stage + C::GOFF), V.fin, V.N, P.nx,
-                                   P.ny, d0.x0, d0.y0};
-    // after the tile's barrier its stage is free: refill it with the next
-    // tile this stage serves
-    const int tn = STAGES == 2 ? t2 : t1;
+    const StageSrc<SH, TG, NS, SG> src{(const float*)(stage + C::FOFF),
+                                       SG ? (const TG*)(stage + C::GOFF) : V.gin, V.fin, V.N, P.nx, P.ny, d0.x0, d0.y0};
+    // after the tile's barrier: MODE 1 refills this tile's stage with tile
+    // j+2; MODE 2 refills the other stage (tile j-1 is done with it: every
+    // thread has passed this barrier) with tile j+1, from the second tile on
     auto refill = [&] {
-      if (threadIdx.x == 0 && tn < ntiles) issue(SINGLE ? (STAGES == 2 ? d2 : d1) : tiles[tn], stage, &bars[b]);
+      if (threadIdx.x != 0) return;
+      if constexpr (MODE == 1) {
+        if (t2 < ntiles) issue(SINGLE ? d2 : tiles[t2], stage, &bars[b]);
+      } else {
+        if (j >= 1 && t1 < ntiles) issue(SINGLE ? d1 : tiles[t1], dyn + (b ^ 1) * C::STAGE, &bars[b ^ 1]);
+      }
     };
     auto next_types = [&](TileTypes& t) {
       if (t1 < ntiles)
@@ -956,13 +1002,14 @@ __global__ void __launch_bounds__(NTHREADS, STAGES == 2 ? 2 : 3)
     if (bulk_tile<SH, float, TG, R, NS>(d0, V, P, src, refill, next_types, ok, tt, acc, s_pot[sb], s_t[sb],
                                         s_m[sb])) {
       // a wait gave up: record it, let the copies still in flight land
-      // (bounded waits: this tile's stage, and with two stages the next
-      // tile's), and leave
+      // (bounded waits: this tile's stage, and the other stage when it holds
+      // a copy not waited for yet: always in MODE 1 (tile j+1), in MODE 2
+      // only on the first tile (tile 1, issued up front)), and leave
       flush_acc(acc, V.scal, V.cur);
       if (threadIdx.x == 0) {
         atomicOr(&V.scal[S_STATUS], (unsigned long long)ST_TIMEOUT);
         mbar_wait_bounded(&bars[b], ((phase >> b) & 1u) ^ 1u);
-        if (STAGES == 2 && t1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
+        if ((MODE == 1 || j == 0) && t1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
       }
       return;
     }

@@ -35,13 +35,12 @@ void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts,
 // Staged variants: grid of as many blocks as fit (two per SM with the
 // double-buffered stage, three with the single stage), dynamic shared memory
 // opted in once.
-template <class SH, int SHAPE, int NS, int STAGES, bool SINGLE>
+template <class SH, int SHAPE, int NS, int MODE, bool SINGLE>
 int bulk_tma_cap() {
-  using C = StageCfg<SH, KTG, NS>;
-  constexpr int smem = STAGES * C::STAGE;
+  constexpr int smem = tma_smem<SH, KTG, NS, MODE>();
   static int cap = 0;
   if (cap == 0) {
-    auto k = k_bulk_tma<SH, SHAPE, KTG, NS, STAGES, SINGLE>;
+    auto k = k_bulk_tma<SH, SHAPE, KTG, NS, MODE, SINGLE>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -53,19 +52,18 @@ int bulk_tma_cap() {
 }
 // single: the parameter block of the only simulation of the tile list (host
 // copy, passed by value), or null for a batch.
-template <class SH, int SHAPE, int NS, int STAGES>
+template <class SH, int SHAPE, int NS, int MODE>
 void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts, const DevParams* single) {
   if (ntiles <= 0) return;
-  using C = StageCfg<SH, KTG, NS>;
-  constexpr int smem = STAGES * C::STAGE;
+  constexpr int smem = tma_smem<SH, KTG, NS, MODE>();
   if (single) {
-    const int cap = bulk_tma_cap<SH, SHAPE, NS, STAGES, true>();
-    k_bulk_tma<SH, SHAPE, KTG, NS, STAGES, true>
+    const int cap = bulk_tma_cap<SH, SHAPE, NS, MODE, true>();
+    k_bulk_tma<SH, SHAPE, KTG, NS, MODE, true>
         <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, *single);
   } else {
     static const DevParams unused{};
-    const int cap = bulk_tma_cap<SH, SHAPE, NS, STAGES, false>();
-    k_bulk_tma<SH, SHAPE, KTG, NS, STAGES, false>
+    const int cap = bulk_tma_cap<SH, SHAPE, NS, MODE, false>();
+    k_bulk_tma<SH, SHAPE, KTG, NS, MODE, false>
         <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, unused);
   }
 }
@@ -115,8 +113,8 @@ template <int NS>
 constexpr Launchers make() {
   if constexpr (sizeof(KTF) == 4) {
     return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>},
-                     {&bulk_tma_l<ShapeA, 0, NS, 2>, &bulk_tma_l<ShapeB, 1, NS, 2>},
                      {&bulk_tma_l<ShapeA, 0, NS, 1>, &bulk_tma_l<ShapeB, 1, NS, 1>},
+                     {&bulk_tma_l<ShapeA, 0, NS, 2>, &bulk_tma_l<ShapeB, 1, NS, 2>},
                      &vop_l<NS>,
                      &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
   } else {

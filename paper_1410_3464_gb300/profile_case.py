@@ -35,7 +35,7 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SHAPES = ((16, 16), (32, 8))
 STAGINGS = (0, 1, 2)
-STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma 1-stage"}
+STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma d2q9-box"}
 WORKLOAD = "porous discs 1024x512 (seed 1), FP32, 3 species"
 
 

@@ -36,7 +36,7 @@ import numpy as np
 from . import inputs, pslbm
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma 1-stage"}
+STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma d2q9-box"}
 
 
 def peak_gbs():
