@@ -91,16 +91,6 @@ __device__ __forceinline__ TileTypes load_types(const Tile& tl, const DevParams&
   return tt;
 }
 
-// The same for a tile of any instance of a batch (the instance's current
-// type buffer found through its step counter).
-template <class SH>
-__device__ __forceinline__ TileTypes load_types(const Tile* tiles, const DevInst* insts, int ti, int tid) {
-  const Tile tl = tiles[ti];
-  const DevInst* Ip = insts + tl.inst;
-  const int cur = int(Ip->scal[S_STEP] & 1ULL);
-  return load_types<SH>(tl, Ip->P, Ip->type[cur], tid);
-}
-
 // What one bulk launch needs of an instance: the buffers of the current step,
 // the step and the liquid threshold.  All are fixed for the launch (the step
 // counter and the threshold advance in the amendment kernel), so a launch over
@@ -348,16 +338,6 @@ template <class R> __device__ __forceinline__ int code_of(R v);
 template <> __device__ __forceinline__ int code_of<float>(float v) { return __float_as_int(v); }
 template <> __device__ __forceinline__ int code_of<double>(double v) { return (int)__double_as_longlong(v); }
 
-// First tile at or after ti (stride `stride`) whose instance is not frozen at
-// its step limit; ntiles if none.
-__device__ __forceinline__ int next_live(const Tile* tiles, int ntiles, const DevInst* insts, int ti, int stride) {
-  for (; ti < ntiles; ti += stride) {
-    const DevInst* I = insts + tiles[ti].inst;
-    if (I->scal[S_STEP] < I->scal[S_LIMIT]) break;
-  }
-  return ti;
-}
-
 // Population source of the plain kernel: loads from global memory (L2 for
 // the ring).  own() loads the node's D2Q9 and D2Q5 populations (as stored,
 // i.e. shifted in the reduced precisions); ring_density() returns the two
@@ -418,8 +398,11 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   const uint8_t* __restrict__ tin = V.tin;
   uint8_t* __restrict__ tout = V.tout;
   const R theta = V.theta;
-  // tiles whose ring is inside the domain need no wrap arithmetic
-  const bool inner = tl.x0 >= 1 && tl.y0 >= 1 && tl.x0 + SH::TX + 1 <= nx && tl.y0 + SH::TY + 1 <= P.ny;
+  // neighbour indices need wrap arithmetic only on a tile whose ring crosses
+  // a periodic edge: across a non-periodic edge the neighbour is a wall, and
+  // a push toward a wall bounces back without using the neighbour's index
+  const bool inner = (!P.px || (tl.x0 >= 1 && tl.x0 + SH::TX + 1 <= nx)) &&
+                     (!P.py || (tl.y0 >= 1 && tl.y0 + SH::TY + 1 <= P.ny));
   unsigned status = 0;
 
   // ---- phase 1: population loads (own node and one ring node)
@@ -730,8 +713,9 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
 //
 // SINGLE: every tile belongs to the one simulation at insts[0]; its step view
 // is read once, the next tile's descriptor is loaded a tile ahead, and the
-// maximum and status are flushed once at the end.  Otherwise each tile's
-// instance supplies its own view and the accumulators are flushed per tile.
+// maximum and status are flushed once at the end.  Otherwise (a batch) the
+// view and step limit are read, and the accumulators flushed, once per run of
+// consecutive tiles of one instance.
 template <class SH, class TF, class TG, class R, int NS, bool SINGLE>
 __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const Tile* __restrict__ tiles, int ntiles,
                                                                          const DevInst* __restrict__ insts) {
@@ -764,23 +748,44 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
     }
     flush_acc(acc, V.scal, V.cur);
   } else {
-    int ti = next_live(tiles, ntiles, insts, blockIdx.x, stride);
-    if (ti < ntiles) tt = load_types<SH>(tiles, insts, ti, threadIdx.x);
+    // a batch: consecutive tiles of a block often belong to one instance (a
+    // large member spans many grid strides), so the instance's view and step
+    // limit are read, and its maximum and status flushed, only when the
+    // instance changes; tile descriptors ride a tile ahead
+    int ti = blockIdx.x;
+    Tile tl = ti < ntiles ? tiles[ti] : Tile{};
+    int vinst = -1;            // instance of the run in progress
+    bool vlive = false;        // ... below its step limit
+    bool have_tt = false;      // tt holds the current tile's types
+    StepView<TF, TG, R> V{};
     while (ti < ntiles) {
-      const int nt = next_live(tiles, ntiles, insts, ti + stride, stride);
-      const Tile tl = tiles[ti];
-      const DevInst* Ip = insts + tl.inst;
-      const StepView<TF, TG, R> V = step_view<TF, TG, R>(Ip);
-      const GlobalSrc<TF, TG, R, NS> src{V.fin, V.gin, V.N};
-      auto next_types = [&](TileTypes& t) {
-        if (nt < ntiles) t = load_types<SH>(tiles, insts, nt, threadIdx.x);
-      };
-      bulk_tile<SH, TF, TG, R, NS>(tl, V, Ip->P, src, [] {}, next_types, true, tt, acc, s_pot[buf], s_t[buf],
-                                   s_m[buf]);
-      flush_acc(acc, V.scal, V.cur);
-      buf ^= 1;
+      const int nt = ti + stride;
+      const Tile tn = nt < ntiles ? tiles[nt] : Tile{};
+      if (tl.inst != vinst) {
+        if (vlive) flush_acc(acc, V.scal, V.cur);
+        vinst = tl.inst;
+        const DevInst* I = insts + vinst;
+        vlive = I->scal[S_STEP] < I->scal[S_LIMIT];
+        if (vlive) V = step_view<TF, TG, R>(I);
+        have_tt = false;
+      }
+      if (vlive) {
+        const DevParams& P = insts[vinst].P;
+        if (!have_tt) tt = load_types<SH>(tl, P, V.tin, threadIdx.x);
+        const bool same = nt < ntiles && tn.inst == vinst;
+        auto next_types = [&](TileTypes& t) {
+          if (same) t = load_types<SH>(tn, P, V.tin, threadIdx.x);
+        };
+        const GlobalSrc<TF, TG, R, NS> src{V.fin, V.gin, V.N};
+        bulk_tile<SH, TF, TG, R, NS>(tl, V, P, src, [] {}, next_types, true, tt, acc, s_pot[buf], s_t[buf],
+                                     s_m[buf]);
+        buf ^= 1;
+        have_tt = same;
+      }
       ti = nt;
+      tl = tn;
     }
+    if (vlive) flush_acc(acc, V.scal, V.cur);
   }
 }
 
@@ -905,6 +910,16 @@ __device__ __forceinline__ void stage_issue(const Tile& d, const CUtensorMap* mf
 //     (fewer registers, 70 KB of shared memory).  The stage of tile j is read
 //     until the end of tile j, so the copy of tile j+1 goes into tile j-1's
 //     stage right after tile j's barrier.
+// Blocks walk the tile list with the grid stride; tile descriptors ride two
+// tiles ahead in registers.  SINGLE: every tile belongs to the one simulation
+// at insts[0], whose parameter block comes as a kernel argument (read from the
+// constant bank, uniform across the grid); its step view and population maps
+// are read once and the maximum and status flushed once at the end.
+// Otherwise (a batch) the view and step limit are read, the population maps
+// acquired and the accumulators flushed once per run of consecutive tiles of
+// one instance; tiles of a member frozen at its step limit are copied but not
+// computed.
+//
 // Smem bytes of the dynamic stages of a mode.
 template <class SH, class TG, int NS, int MODE>
 constexpr int tma_smem() {
@@ -925,104 +940,125 @@ __global__ void __launch_bounds__(NTHREADS, MODE == 1 ? 2 : 3)
   __shared__ __align__(8) uint64_t bars[2];
 
   const int stride = gridDim.x;
-  View V1{};
+  View V{};
   if constexpr (SINGLE) {
     // one simulation: all tiles are live or none is
     if (!(insts->scal[S_STEP] < insts->scal[S_LIMIT])) return;
-    V1 = step_view<float, TG, R>(insts);
+    V = step_view<float, TG, R>(insts);
   }
-  auto live = [&](int t) { return SINGLE ? (t < ntiles ? t : ntiles) : next_live(tiles, ntiles, insts, t, stride); };
+  // the instance whose population maps the issuing thread acquired last (batch)
+  int iss_inst = -1, iss_cur = 0;
   // copies of a tile into a stage (thread 0)
   auto issue = [&](const Tile& d, unsigned char* stage, uint64_t* bar) {
     const DevInst* Ip = insts + (SINGLE ? 0 : d.inst);
-    const int cur = SINGLE ? V1.cur : int(Ip->scal[S_STEP] & 1ULL);
-    const CUtensorMap* mf = &Ip->tmf[SHAPE][cur];
-    const CUtensorMap* mg = &Ip->tmg[SHAPE][cur];
+    int cur = V.cur;
     if constexpr (!SINGLE) {
-      tensormap_acquire(mf);
-      if constexpr (NS > 0 && SG) tensormap_acquire(mg);
+      if (d.inst != iss_inst) {
+        iss_inst = d.inst;
+        iss_cur = int(Ip->scal[S_STEP] & 1ULL);
+        tensormap_acquire(&Ip->tmf[SHAPE][iss_cur]);
+        if constexpr (NS > 0 && SG) tensormap_acquire(&Ip->tmg[SHAPE][iss_cur]);
+      }
+      cur = iss_cur;
     }
-    stage_issue<SH, TG, NS, SG>(d, mf, mg, stage, bar);
+    stage_issue<SH, TG, NS, SG>(d, &Ip->tmf[SHAPE][cur], &Ip->tmg[SHAPE][cur], stage, bar);
   };
-  int ti = live(blockIdx.x);
-  int t1 = ti < ntiles ? live(ti + stride) : ntiles;
-  // one simulation: tile descriptors ride a tile ahead in registers; a batch
-  // loads them where they are used (fewer live registers on its longer path)
+  // tile descriptors ride two tiles ahead in registers
+  int ti = blockIdx.x;
+  int t1 = ti + stride;
   Tile d0 = ti < ntiles ? tiles[ti] : Tile{};
-  Tile d1 = SINGLE && t1 < ntiles ? tiles[t1] : Tile{};
+  Tile d1 = t1 < ntiles ? tiles[t1] : Tile{};
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_barrier_init();
     if constexpr (SINGLE) {
-      tensormap_acquire(&insts->tmf[SHAPE][V1.cur]);
-      if constexpr (NS > 0 && SG) tensormap_acquire(&insts->tmg[SHAPE][V1.cur]);
+      tensormap_acquire(&insts->tmf[SHAPE][V.cur]);
+      if constexpr (NS > 0 && SG) tensormap_acquire(&insts->tmg[SHAPE][V.cur]);
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (ti < ntiles) issue(d0, dyn, &bars[0]);
-    if (t1 < ntiles) issue(SINGLE ? d1 : tiles[t1], dyn + C::STAGE, &bars[1]);
+    if (t1 < ntiles) issue(d1, dyn + C::STAGE, &bars[1]);
   }
   TileTypes tt;
-  if (ti < ntiles)
-    tt = SINGLE ? load_types<SH>(d0, Pk, V1.tin, threadIdx.x) : load_types<SH>(tiles, insts, ti, threadIdx.x);
+  bool have_tt = false;             // tt holds the current tile's types
+  int vinst = SINGLE ? 0 : -1;      // instance of the run in progress (batch)
+  bool vlive = SINGLE;              // ... below its step limit
   TileAcc<R> acc{R(-1.0 / 0.0), 0u};
   int j = 0;                        // tiles processed by this block
   uint32_t phase = 0;               // parity bit per stage
   while (ti < ntiles) {
-    const int b = j & 1;                          // stage of this tile
-    const int sb = j & 1;                         // shared buffers of this tile
-    const int t2 = t1 < ntiles ? live(t1 + stride) : ntiles;
-    const Tile d2 = SINGLE && t2 < ntiles ? tiles[t2] : Tile{};
+    const int b = j & 1;                          // stage and shared buffers of this tile
+    const int t2 = t1 + stride;
+    const Tile d2 = t2 < ntiles ? tiles[t2] : Tile{};
     const bool ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
     phase ^= 1u << b;
-    if constexpr (!SINGLE) d0 = tiles[ti];
-    const DevInst* Ip = insts + (SINGLE ? 0 : d0.inst);
-    const View V = SINGLE ? V1 : step_view<float, TG, R>(Ip);
+    if constexpr (!SINGLE) {
+      if (d0.inst != vinst) {
+        // a new run of tiles of one instance: close the previous one and read
+        // this instance's view once
+        if (vlive) flush_acc(acc, V.scal, V.cur);
+        vinst = d0.inst;
+        const DevInst* I = insts + vinst;
+        vlive = I->scal[S_STEP] < I->scal[S_LIMIT];
+        if (vlive) V = step_view<float, TG, R>(I);
+        have_tt = false;
+      }
+    }
     unsigned char* stage = dyn + b * C::STAGE;
-    const DevParams& P = SINGLE ? Pk : Ip->P;
-    const StageSrc<SH, TG, NS, SG> src{(const float*)(stage + C::FOFF),
-                                       SG ? (const TG*)(stage + C::GOFF) : V.gin, V.fin, V.N, P.nx, P.ny, d0.x0, d0.y0};
     // after the tile's barrier: MODE 1 refills this tile's stage with tile
     // j+2; MODE 2 refills the other stage (tile j-1 is done with it: every
     // thread has passed this barrier) with tile j+1, from the second tile on
     auto refill = [&] {
       if (threadIdx.x != 0) return;
       if constexpr (MODE == 1) {
-        if (t2 < ntiles) issue(SINGLE ? d2 : tiles[t2], stage, &bars[b]);
+        if (t2 < ntiles) issue(d2, stage, &bars[b]);
       } else {
-        if (j >= 1 && t1 < ntiles) issue(SINGLE ? d1 : tiles[t1], dyn + (b ^ 1) * C::STAGE, &bars[b ^ 1]);
+        if (j >= 1 && t1 < ntiles) issue(d1, dyn + (b ^ 1) * C::STAGE, &bars[b ^ 1]);
       }
     };
-    auto next_types = [&](TileTypes& t) {
-      if (t1 < ntiles)
-        t = SINGLE ? load_types<SH>(d1, Pk, V1.tin, threadIdx.x) : load_types<SH>(tiles, insts, t1, threadIdx.x);
-    };
-    if (bulk_tile<SH, float, TG, R, NS>(d0, V, P, src, refill, next_types, ok, tt, acc, s_pot[sb], s_t[sb],
-                                        s_m[sb])) {
+    bool stop;
+    if (vlive) {
+      const DevParams& P = SINGLE ? Pk : insts[vinst].P;
+      if (!have_tt) tt = load_types<SH>(d0, P, V.tin, threadIdx.x);
+      const bool same = t1 < ntiles && (SINGLE || d1.inst == vinst);
+      auto next_types = [&](TileTypes& t) {
+        if (same) t = load_types<SH>(d1, P, V.tin, threadIdx.x);
+      };
+      const StageSrc<SH, TG, NS, SG> src{(const float*)(stage + C::FOFF),
+                                         SG ? (const TG*)(stage + C::GOFF) : V.gin, V.fin, V.N, P.nx, P.ny, d0.x0,
+                                         d0.y0};
+      stop = bulk_tile<SH, float, TG, R, NS>(d0, V, P, src, refill, next_types, ok, tt, acc, s_pot[b], s_t[b],
+                                             s_m[b]);
+      have_tt = same;
+    } else {
+      // a member frozen at its step limit: its copy landed, nothing to
+      // compute; once every thread is past its wait the stage may be reused
+      stop = __syncthreads_or(ok ? 0 : 1) != 0;
+      if (!stop) refill();
+    }
+    if (stop) {
       // a wait gave up: record it, let the copies still in flight land
       // (bounded waits: this tile's stage, and the other stage when it holds
       // a copy not waited for yet: always in MODE 1 (tile j+1), in MODE 2
       // only on the first tile (tile 1, issued up front)), and leave
-      flush_acc(acc, V.scal, V.cur);
+      if (vlive) flush_acc(acc, V.scal, V.cur);
       if (threadIdx.x == 0) {
-        atomicOr(&V.scal[S_STATUS], (unsigned long long)ST_TIMEOUT);
+        atomicOr(&insts[SINGLE ? 0 : d0.inst].scal[S_STATUS], (unsigned long long)ST_TIMEOUT);
         mbar_wait_bounded(&bars[b], ((phase >> b) & 1u) ^ 1u);
         if ((MODE == 1 || j == 0) && t1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], (phase >> (b ^ 1)) & 1u);
       }
       return;
     }
-    if constexpr (!SINGLE) flush_acc(acc, V.scal, V.cur);
     ++j;
     ti = t1;
     t1 = t2;
-    if constexpr (SINGLE) {
-      d0 = d1;
-      d1 = d2;
-    }
+    d0 = d1;
+    d1 = d2;
   }
-  if constexpr (SINGLE) flush_acc(acc, V1.scal, V1.cur);
+  if (vlive) flush_acc(acc, V.scal, V.cur);
 }
 
 }  // namespace pslbm

@@ -4,7 +4,7 @@ what ncu measured on it.
     python -m paper_1410_3464_gb300.profile_case run [--warm 2] [--steps 3] [--only SHAPE:STAGING]
         porous discs 1024x512 (seed 1), FP32, three transported species: the
         bulk-kernel variants (tile 16x16 and 32x8, each with plain loads, TMA
-        2-stage and TMA 1-stage staging) in that order, each for --warm then
+        2-stage and TMA D2Q9-box staging) in that order, each for --warm then
         --steps single steps.  The working set (about 150 MB) is larger than
         the 129 MB L2, so DRAM counters mean something, and small enough for a
         multi-pass ncu capture.
