@@ -256,6 +256,33 @@ def profile_traffic(workload, variant):
     return pj.get("traffic_per_launch", {}).get(variant)
 
 
+# GB300's nominal FP64 rate: 152 SMs x 2.07 GHz x 2 FP64 FMA per clock x 2 flops
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
+
+
+def fp64_roofline(workload, variant, kernel_ms):
+    """FP64-ALU roofline of the FP64 bulk kernel: the FP64 operations one launch
+    executes (ncu count from the committed summary of the same kernel variant
+    built from the same sources) per launch time, against the nominal FP64
+    rate.  None without a matching summary."""
+    from paper_1410_3464_gb300 import profile_case
+    path = os.path.join(ROOT, "profiles", f"k_bulk_{PROFILE_TAGS[workload]}_fp64.json")
+    if not os.path.exists(path):
+        return None
+    pj = json.load(open(path))
+    if pj.get("source_hash") != profile_case.kernel_source_hash("fp64"):
+        return None
+    flops = pj.get("fp64_flops_per_launch", {}).get(variant)
+    if not flops:
+        return None
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_bulk<double>", "variant": variant,
+            "flops_per_launch": flops, "kernel_ms": kernel_ms,
+            "peak_source": "nominal GB300 FP64 rate (152 SMs x 2.07 GHz x 2 FMA/clock x 2 flops)",
+            "fp64_pipe_active_pct_ncu": pj.get("fp64_pipe_active_pct", {}).get(variant)}
+
+
 def ours_arm(args):
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
@@ -363,6 +390,13 @@ def ours_arm(args):
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
                 else "fallback 6.8 TB/s",
                 "kernel_share": bulk_ms / statistics.mean(tot)}
+    if prec == pslbm.FP64:
+        # the FP64 path is bound by FP64 arithmetic, not by HBM
+        alu = fp64_roofline(args.workload, variant, bulk_ms)
+        if alu is not None:
+            alu["kernel_share"] = roofline["kernel_share"]
+            alu["hbm"] = {k: roofline[k] for k in ("achieved", "peak", "unit", "frac", "bytes_per_launch")}
+            roofline = alu
 
     cfg = {"workload": WORKLOAD_NAMES[args.workload], "members": len(scenes), "nodes": N,
            "fluid_nodes": n_fluid, "liquid_nodes": n_liq, "precision": args.precision,

@@ -39,11 +39,12 @@ STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma d2q9-box"}
 WORKLOAD = "porous discs 1024x512 (seed 1), FP32, 3 species"
 
 
-def kernel_source_hash():
-    """Hash of the device sources the FP32 bulk kernels are compiled from."""
+def kernel_source_hash(precision="fp32"):
+    """Hash of the device sources the bulk kernels of a precision are compiled from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1410_3464_gb300", "csrc")
-    for f in ("device.cuh", "tma.cuh", "bulk.cuh", "kernels_impl.cuh", "kernels_f32.cu"):
+    unit = {"fp32": "kernels_f32.cu", "fp64": "kernels_f64.cu"}[precision]
+    for f in ("device.cuh", "tma.cuh", "bulk.cuh", "kernels_impl.cuh", unit):
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
@@ -104,11 +105,13 @@ def run(args):
         return run_batch(args)
     from . import inputs, pslbm
     sc = inputs.porous_discs(nx=1024, ny=512, seed=1)
+    prec = pslbm.FP64 if args.fp64 else pslbm.FP32
     with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
-                          precision=pslbm.FP32) as sim:
-        if not sim.staging()[1]:
+                          precision=prec) as sim:
+        if not args.fp64 and not sim.staging()[1]:
             raise SystemExit("TMA staging unavailable on this device")
-        for shape, g in variants(args.only):
+        vs = [v for v in variants(args.only) if not (args.fp64 and v[1] != 0)]
+        for shape, g in vs:
             sim.set_tile_shape(*shape)
             sim.set_staging(g)
             for _ in range(args.warm + args.steps):
@@ -141,7 +144,9 @@ def read_launches(path):
 def summarize(args):
     rows = read_launches(args.csv)
     bulk = [rows[k] for k in sorted(rows) if "k_bulk" in rows[k][0]]
-    vs = variants(args.only)
+    vs = [v for v in variants(args.only) if not (args.fp64 and v[1] != 0)]
+    if args.fp64:
+        return summarize_fp64(args, bulk, vs)
     per = args.warm + args.steps
     if len(bulk) != per * len(vs):
         raise SystemExit(f"expected {per * len(vs)} bulk launches, found {len(bulk)}")
@@ -186,6 +191,36 @@ def summarize(args):
     return 0
 
 
+def summarize_fp64(args, bulk, vs):
+    """FP64 operations per launch of the FP64 bulk kernel (plain loads): 2 per
+    DFMA, 1 per DADD and DMUL, counted by ncu over the executed thread
+    instructions, and the FP64 pipe's active share."""
+    per = args.warm + args.steps
+    if len(bulk) != per * len(vs):
+        raise SystemExit(f"expected {per * len(vs)} bulk launches, found {len(bulk)}")
+    out = {"kernel": "k_bulk<double> (plain loads), FP64, 3 species, single simulation",
+           "workload": "porous discs 1024x512 (seed 1), FP64, 3 species", "source_hash": kernel_source_hash("fp64"),
+           "fp64_flops_per_launch": {}, "fp64_pipe_active_pct": {}, "ncu_duration_us": {},
+           "note": ("FP64 operations counted by ncu over executed thread instructions (DFMA as 2, DADD and DMUL as "
+                    f"1), means over the {args.steps} launches after {args.warm} warm-up launches"),
+           "command": args.command}
+    for i, (shape, g) in enumerate(vs):
+        launches = bulk[i * per + args.warm:(i + 1) * per]
+        fl = statistics.mean(2 * m["sm__sass_thread_inst_executed_op_dfma_pred_on.sum"] +
+                             m["sm__sass_thread_inst_executed_op_dadd_pred_on.sum"] +
+                             m["sm__sass_thread_inst_executed_op_dmul_pred_on.sum"] for _, m in launches)
+        key = variant_name(shape, g)
+        out["fp64_flops_per_launch"][key] = int(round(fl))
+        out["fp64_pipe_active_pct"][key] = round(statistics.mean(
+            m["sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active"] for _, m in launches), 2)
+        out["ncu_duration_us"][key] = round(statistics.mean(m["gpu__time_duration.sum"] for _, m in launches) * 1e6, 2)
+    with open(args.out, "w") as fh:
+        json.dump(out, fh, indent=1)
+        fh.write("\n")
+    print(json.dumps(out["fp64_flops_per_launch"]))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -195,6 +230,7 @@ def main(argv=None):
         p.add_argument("--steps", type=int, default=3)
         p.add_argument("--only", default=None, help="one variant, e.g. 32x8:1")
         p.add_argument("--batch", type=int, default=0, help="members of the benchmark batch (0: one lattice)")
+        p.add_argument("--fp64", action="store_true", help="the FP64 path (plain-load variants only)")
         if name == "summarize":
             p.add_argument("--alg-small", type=int, default=0, help="algorithmic bytes per launch of the run")
             p.add_argument("--alg-full", type=int, default=0, help="algorithmic bytes per launch of the full batch")
