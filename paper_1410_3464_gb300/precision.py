@@ -69,7 +69,8 @@ def scene(args):
         sc = inputs.bubble_grain(nx=args.nx, ny=args.ny, grain=(args.nx // 2, args.ny // 2, args.ny * 3 // 16),
                                  bubble=(args.nx * 3 // 16, args.ny // 2, args.ny * 5 // 32))
     else:
-        sc = inputs.porous_discs(nx=args.nx, ny=args.ny, seed=args.seed, bubbles=args.bubbles)
+        sc = inputs.porous_discs(nx=args.nx, ny=args.ny, seed=args.seed, bubbles=args.bubbles,
+                                 gas_yield=not args.no_gas_yield)
     p = dict(sc["params"])
     if args.rho_ref is not None:
         p["rho_ref"] = tuple(float(v) for v in args.rho_ref.split(","))
@@ -132,7 +133,7 @@ def study(args):
                                     for g, r in zip(got["budget"][:-1], ref["budget"][:-1])]
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
-        if args.save_fields:
+        if args.save_fields and c in args.save_at:
             np.savez_compressed(f"{args.save_fields}_{c}.npz", **{f"{p}_{k}": v for p in ["fp64"] + precs if p in sims
                                 for k, v in sims[p].read().items()})
     for s in sims.values():
@@ -151,12 +152,16 @@ def main(argv=None):
     ap.add_argument("--steps", default="100,1000,10000")
     ap.add_argument("--precisions", default="fp32,fp32_f16,fp32_bf16")
     ap.add_argument("--save-fields", default=None, help="path prefix: save all fields at each checkpoint")
+    ap.add_argument("--save-at", default="", help="checkpoints to save fields at (default: all)")
     ap.add_argument("--bubbles", type=int, default=None, help="gas bubbles seeded in the porous scene")
+    ap.add_argument("--no-gas-yield", action="store_true",
+                    help="porous scene without R1's gas product (stable on long lattices)")
     ap.add_argument("--rho-ref", default=None, help="population shift per fluid component, e.g. 0,0")
     ap.add_argument("--conc-ref", default=None, help="solute population shift per species, e.g. 0,0,0")
     ap.add_argument("--perturb", type=float, default=0.0,
                     help="also run FP64 from rho_1 perturbed by this relative size (flow sensitivity)")
     args = ap.parse_args(argv)
+    args.save_at = {int(v) for v in args.save_at.split(",") if v} or {int(v) for v in args.steps.split(",")}
     print(json.dumps(study(args)))
 
 

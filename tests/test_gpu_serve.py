@@ -148,3 +148,29 @@ def test_server_isolates_a_failing_request(pslbm):
     for k in FIELDS:
         assert np.array_equal(got[k], ref[k]), k
     srv.close()
+
+
+def test_batch_monitor_and_profile(pslbm):
+    """pslbm_batch_monitor gathers every member's step count and status in one
+    read; pslbm_batch_profile_step times the three kernels of each step and
+    advances the members like pslbm_batch_step (same results)."""
+    scs = [inputs.porous_discs(nx=64 + 16 * i, ny=48, seed=20 + i) for i in range(3)]
+    refs = [alone(pslbm, sc, 12, pslbm.FP32) for sc in scs]
+    sims = [pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                             precision=pslbm.FP32) for sc in scs]
+    sims[1].set_step_limit(7)
+    b = pslbm.Batch(sims)
+    b.step(5)
+    assert b.monitor() == (5, 0)
+    k, total = b.profile_step(7)
+    assert all(v > 0 for v in k.values()) and total >= k["bulk"]
+    steps, status = b.monitor()
+    assert steps == 7 and status == 0          # the smallest step count: member 1 froze at 7
+    b.close()
+    for i, (s, ref) in enumerate(zip(sims, refs)):
+        assert s.steps() == (7 if i == 1 else 12)
+        if i != 1:
+            got = s.read()
+            for f in FIELDS:
+                assert np.array_equal(got[f], ref[f]), f
+        s.close()
