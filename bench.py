@@ -315,7 +315,7 @@ def ours_arm(args):
     trials = None
     if batch:
         runner = pslbm.Batch(sims)
-        runner.step(30)              # variant autotuning (6 variants x 4 steps) and a first warm-up
+        runner.step(45)              # variant autotuning (10 variants x 4 steps) and a first warm-up
     else:
         # one lattice: each variant timed for 5 steps under the timed loop's own
         # conditions (L2 flushed before every step for the 1024x512 lattice)
@@ -323,8 +323,11 @@ def ours_arm(args):
         trials = {}
         stagings = [0, 1, 2] if runner.staging()[1] else [0]
         with torch.cuda.stream(stream):
-            for shape in ((16, 16), (32, 8)):
+            for shape in ((16, 16), (32, 8), (16, 32), (32, 16)):
                 for sg in stagings:
+                    if sg == 1 and shape[0] * shape[1] > 256:
+                        continue     # two nodes per thread: no staging 1
+                    runner.set_staging(-1)
                     runner.set_tile_shape(*shape)
                     runner.set_staging(sg)
                     ts = []
@@ -335,6 +338,7 @@ def ours_arm(args):
                     trials[(shape, sg)] = statistics.median(ts[1:])
         torch.cuda.synchronize()
         best = min(trials, key=trials.get)
+        runner.set_staging(-1)
         runner.set_tile_shape(*best[0])
         runner.set_staging(best[1])
     runner.step(args.warmup)         # warm-up with the chosen variant

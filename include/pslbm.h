@@ -196,24 +196,30 @@ pslbm_status pslbm_set_step_limit(pslbm_t h, int64_t limit);
  * the read-back scratch of pslbm_read_fields). */
 pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes);
 
-/* Tile shape of the step kernels: 16x16 or 32x8 nodes per 256-thread block.
+/* Tile shape of the step kernels, which also sets the nodes per thread of a
+ * 256-thread block: 16x16 or 32x8 (one node per thread), 16x32 or 32x16 (two
+ * nodes per thread: thread (tx, ty) computes rows ty and ty + 256 / tile_x).
  * (0, 0), the default, leaves the shape to timing: the next step call long
  * enough to try every open variant (tile shape x staging, 4 steps each, which
  * advance the simulation like any others) times them and keeps the fastest;
  * the results do not depend on the variant.  tuned reports whether the variant
- * has been chosen (by timing, or because only one was left open). */
+ * has been chosen (by timing, or because only one was left open).
+ * PSLBM_ERR_PARAM for another shape, or for a two-node shape while staging 1
+ * is fixed (the handle is left as it was). */
 pslbm_status pslbm_set_tile_shape(pslbm_t h, int32_t tile_x, int32_t tile_y);
 pslbm_status pslbm_get_tile_shape(pslbm_t h, int32_t* tile_x, int32_t* tile_y, int32_t* tuned);
 
 /* Staging of the bulk kernel's populations: 0 plain per-thread loads; 1 TMA
  * copies of each tile's D2Q9 and D2Q5 population boxes into shared memory two
- * tiles ahead (two stages, two blocks per SM); 2 TMA copies of the D2Q9 box
- * only, one tile ahead, re-read from shared memory where used, with the
- * solute populations loaded directly (two stages, three blocks per SM).  1 and
- * 2 are available for the FP32-population precisions
+ * tiles ahead (two stages, two blocks per SM; one-node tile shapes only); 2
+ * TMA copies of the D2Q9 box only, one tile ahead, re-read from shared memory
+ * where used, with the solute populations loaded directly (two stages; three
+ * blocks per SM with one node per thread, two with two, whose box has no x
+ * halo).  1 and 2 are available for the FP32-population precisions
  * when a row of the lattice is a multiple of 16 bytes (nx a multiple of 4, and
  * of 8 with 16-bit solutes).  -1 (the default) leaves the choice to timing.
- * PSLBM_ERR_PARAM for 1 or 2 where they are not available.  The results are bit-identical either way.  get reports the
+ * PSLBM_ERR_PARAM for 1 or 2 where they are not available, and for 1 while a
+ * two-node tile shape is fixed.  The results are bit-identical either way.  get reports the
  * staging in use and whether staging is available for the handle.  A staged
  * kernel whose copy does not arrive within about a second stops and sets
  * PSLBM_ERR_TIMEOUT (sticky), reported by the next sync or read. */
@@ -269,8 +275,9 @@ pslbm_status pslbm_budget_device_noalloc(pslbm_t h, double* out);
  * A batch steps several simulations (same precision and species count) in
  * one launch per kernel over a packed list of tiles of all members.  The
  * members stay valid handles; they must not be stepped on their own while
- * the batch exists.  tile_x, tile_y choose the tile shape (16x16 or 32x8;
- * 0, 0: time both on the first steps and keep the faster). */
+ * the batch exists.  tile_x, tile_y choose the tile shape (16x16, 32x8,
+ * 16x32 or 32x16, as for pslbm_set_tile_shape; 0, 0: time every open variant
+ * on the first steps and keep the fastest). */
 pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_x, int32_t tile_y,
                                 pslbm_batch_t* out);
 pslbm_status pslbm_batch_step(pslbm_batch_t b, int64_t n);

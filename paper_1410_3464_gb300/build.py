@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpslbm.so")
-SOURCES = ["kernels_f64.cu", "kernels_f32.cu", "kernels_f32h.cu", "kernels_f32b.cu", "runtime.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["kernels_f64.cu", "kernels_f32.cu", "kernels_f32h.cu", "kernels_f32b.cu", "kernels_f64_n2.cu", "kernels_f32_n2.cu",
+           "kernels_f32h_n2.cu", "kernels_f32b_n2.cu", "runtime.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

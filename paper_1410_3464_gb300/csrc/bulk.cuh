@@ -69,18 +69,22 @@ __device__ __forceinline__ uint8_t ext_type(const DevParams& P, const uint8_t* t
   return tin[idx] & T_MASK;
 }
 
-// Types of one tile for this thread: its own ext position and (tid < SH::RING)
-// one ring position.
+// Types of one tile for this thread: its own ext positions (one per node it
+// computes) and (tid < SH::RING) one ring position.
+template <int NPT>
 struct TileTypes {
-  uint8_t own, ring;
-  int own_idx, ring_idx;
+  uint8_t own[NPT], ring;
+  int own_idx[NPT], ring_idx;
 };
 
 template <class SH>
-__device__ __forceinline__ TileTypes load_types(const Tile& tl, const DevParams& P, const uint8_t* tin, int tid) {
-  TileTypes tt;
+__device__ __forceinline__ TileTypes<SH::NPT> load_types(const Tile& tl, const DevParams& P, const uint8_t* tin,
+                                                         int tid) {
+  TileTypes<SH::NPT> tt;
   const int tx = tid % SH::TX, ty = tid / SH::TX;
-  tt.own = ext_type(P, tin, tl.x0, tl.y0, tx + 1, ty + 1, tt.own_idx);
+#pragma unroll
+  for (int k = 0; k < SH::NPT; ++k)
+    tt.own[k] = ext_type(P, tin, tl.x0, tl.y0, tx + 1, ty + 1 + k * SH::RY, tt.own_idx[k]);
   tt.ring = T_WALL;
   tt.ring_idx = -1;
   if (tid < SH::RING) {
@@ -135,6 +139,16 @@ struct TileAcc {
   R mx;
   unsigned status;
 };
+
+// a[k] of a small register array at a run-time index, as a chain of selects
+// over constant indices (the array stays in registers).
+template <int NA, class T>
+__device__ __forceinline__ T pick(const T (&a)[NA], int k) {
+  T v = a[0];
+#pragma unroll
+  for (int i = 1; i < NA; ++i) v = (k == i) ? a[i] : v;
+  return v;
+}
 
 // Warp reduction of the accumulators into the instance's slots: the exact
 // maximum (the atomic only when it can raise the slot) and the status bits.
@@ -306,14 +320,15 @@ __device__ __noinline__ void reservoir_push(const DevParams& P, const uint8_t* t
 }
 
 // Minimum resident blocks per SM the register allocation targets: FP32
-// compute keeps three 256-thread blocks per SM; FP64 (twice the registers per
-// value, bound by FP64 arithmetic anyway) two.
+// compute with one node per thread keeps three 256-thread blocks per SM; two
+// nodes per thread (twice the moments carried across the tile's barrier) and
+// FP64 (twice the registers per value, bound by FP64 arithmetic anyway) two.
 #ifndef PSLBM_BULK_MINB
 #define PSLBM_BULK_MINB 3
 #endif
-template <class R>
+template <class R, int NPT>
 constexpr int bulk_min_blocks() {
-  return sizeof(R) == 8 ? 2 : PSLBM_BULK_MINB;
+  return (sizeof(R) == 8 || NPT > 1) ? 2 : PSLBM_BULK_MINB;
 }
 
 // Shared-memory record of one ext node: psi_1, phi_1, phi_2 (zero where not
@@ -348,12 +363,18 @@ struct GlobalSrc {
   const TF* fin;
   const TG* gin;
   int N;
-  __device__ __forceinline__ void own_f(int idx, R* f1, R* f2) const {
+  // ly: the node's row in its tile (unused here)
+  __device__ __forceinline__ void own_f(int idx, int, R* f1, R* f2) const {
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       f1[a] = ld<R>(fin + a * N + idx);
       f2[a] = ld<R>(fin + (9 + a) * N + idx);
     }
+  }
+  // one component's populations (an L1 hit when re-read within the tile)
+  __device__ __forceinline__ void own_fc(int idx, int, int comp, R* f) const {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] = ld<R>(fin + (comp * 9 + a) * N + idx);
   }
   __device__ __forceinline__ void own_g(int node, R (*gs)[5]) const {
 #pragma unroll
@@ -375,14 +396,22 @@ struct GlobalSrc {
 // The tile's maximum of rho_1 and its status bits go into `acc`.  Returns true
 // when the block must stop (a bounded wait of the staged kernel gave up in
 // some thread).
+//
+// Each thread computes SH::NPT nodes, rows ty + k RY of the tile.  Before the
+// barrier it loads all of them (their loads in flight together) and keeps
+// their moments; after it, the nodes run one after the other through the same
+// code.  The D2Q9 populations are held in registers across the barrier only
+// with one node per thread and a source that does not re-read them (kHold);
+// otherwise the collision reads them again (from the stage, or from L1).
 template <class SH, class TF, class TG, class R, int NS, class Src, class AfterSync, class NextTypes>
 __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG, R>& V, const DevParams& P,
                                           const Src& src, AfterSync after_sync, NextTypes next_types, bool waited_ok,
-                                          TileTypes& tt, TileAcc<R>& acc, Pot<R>* spot, uint8_t* st_,
+                                          TileTypes<SH::NPT>& tt, TileAcc<R>& acc, Pot<R>* spot, uint8_t* st_,
                                           uint8_t* sm_) {
+  constexpr int NPT = SH::NPT;
+  constexpr bool kHold = NPT == 1 && !Src::kReread;
   const int tid = threadIdx.x;
   const int tx = tid % SH::TX, ty = tid / SH::TX;
-  const int eo = (ty + 1) * SH::EXT_X + (tx + 1);
   int er = -1, rex = 0, rey = 0;
   if (tid < SH::RING) {
     ring_pos<SH>(tid, rex, rey);
@@ -405,24 +434,26 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
                      (!P.py || (tl.y0 >= 1 && tl.y0 + SH::TY + 1 <= P.ny));
   unsigned status = 0;
 
-  // ---- phase 1: population loads (own node and one ring node)
-  const int x = tl.x0 + tx, y = tl.y0 + ty;
-  const bool own = x < nx && y < P.ny;
-  const int node = y * nx + x;
-  const uint8_t own_t = tt.own;
+  // ---- phase 1: population loads (own nodes and one ring node)
+  uint8_t own_tv[NPT];
+  int own_iv[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    own_tv[k] = tt.own[k];
+    own_iv[k] = tt.own_idx[k];
+  }
   const uint8_t ring_t = tt.ring;
-  const int own_idx = tt.own_idx, ring_idx = tt.ring_idx;
-  const uint8_t t = own ? own_t : T_WALL;
+  const int ring_idx = tt.ring_idx;
   // populations are stored relative to the reference density of the node's
   // phase (0 in FP64)
-  const R sh1 = fshift<R>(P, 0, own_t), sh2 = fshift<R>(P, 1, own_t);
-  R f1[9], f2[9];
+  R q1[NPT][9], q2[NPT][9];
   R gs[NS > 0 ? NS : 1][5];
-  const bool own_fluid = is_fluid(own_t) && own_idx >= 0;
-  if (own_fluid) src.own_f(own_idx, f1, f2);
+#pragma unroll
+  for (int k = 0; k < NPT; ++k)
+    if (is_fluid(own_tv[k]) && own_iv[k] >= 0) src.own_f(own_iv[k], ty + k * SH::RY, q1[k], q2[k]);
   // solute populations of a liquid node (undoing the species' storage scale,
-  // a power of two: exact); a re-reading source loads them where used
-  auto load_g = [&] {
+  // a power of two: exact); loaded here only when the populations are held
+  auto load_g = [&](bool own, uint8_t own_t, int node) {
     if constexpr (NS > 0) {
       if (own && own_t == T_LIQUID) {
         src.own_g(node, gs);
@@ -435,7 +466,10 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
       }
     }
   };
-  if constexpr (!Src::kReread) load_g();
+  if constexpr (kHold) {
+    const int x = tl.x0 + tx, y = tl.y0 + ty;
+    load_g(x < nx && y < P.ny, own_tv[0], y * nx + x);
+  }
   R r1r = R(0), r2r = R(0);
   if (tid < SH::RING && is_fluid(ring_t)) {
     R d1r, d2r;
@@ -446,37 +480,52 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   // prefetch the next tile's node types
   next_types(tt);
 
-  // ---- moments of the own node (Eq. 9)
-  R rho1 = R(0), rho2 = R(0), d1 = R(0), d2 = R(0), j1x = R(0), j1y = R(0), j2x = R(0), j2y = R(0);
-  if (own_fluid) {
-    d1 = f1[0];
-    d2 = f2[0];
+  // ---- moments of the own nodes (Eq. 9)
+  R rho1v[NPT], rho2v[NPT], d1v[NPT], d2v[NPT], j1xv[NPT], j1yv[NPT], j2xv[NPT], j2yv[NPT];
 #pragma unroll
-    for (int a = 1; a < 9; ++a) {
-      d1 += f1[a];
-      d2 += f2[a];
+  for (int k = 0; k < NPT; ++k) {
+    R rho1 = R(0), rho2 = R(0), d1 = R(0), d2 = R(0), j1x = R(0), j1y = R(0), j2x = R(0), j2y = R(0);
+    if (is_fluid(own_tv[k]) && own_iv[k] >= 0) {
+      const R* f1 = q1[k];
+      const R* f2 = q2[k];
+      d1 = f1[0];
+      d2 = f2[0];
+#pragma unroll
+      for (int a = 1; a < 9; ++a) {
+        d1 += f1[a];
+        d2 += f2[a];
+      }
+      j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
+      j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
+      j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
+      j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
+      rho1 = fshift<R>(P, 0, own_tv[k]) + d1;
+      rho2 = fshift<R>(P, 1, own_tv[k]) + d2;
+      if (!(rho1 == rho1 && rho2 == rho2)) status |= ST_NONFINITE;
     }
-    j1x = (f1[1] - f1[3]) + (f1[5] - f1[6]) + (f1[8] - f1[7]);
-    j1y = (f1[2] - f1[4]) + (f1[5] - f1[8]) + (f1[6] - f1[7]);
-    j2x = (f2[1] - f2[3]) + (f2[5] - f2[6]) + (f2[8] - f2[7]);
-    j2y = (f2[2] - f2[4]) + (f2[5] - f2[8]) + (f2[6] - f2[7]);
-    rho1 = sh1 + d1;
-    rho2 = sh2 + d2;
-    if (!(rho1 == rho1 && rho2 == rho2)) status |= ST_NONFINITE;
+    rho1v[k] = rho1;
+    rho2v[k] = rho2;
+    d1v[k] = d1;
+    d2v[k] = d2;
+    j1xv[k] = j1x;
+    j1yv[k] = j1y;
+    j2xv[k] = j2x;
+    j2yv[k] = j2y;
   }
-  // ---- potentials of the own node and (tid < RING) one ring node -> shared.
-  // One loop body, not unrolled, serves both, so the equation of state, the
+  // ---- potentials of the own nodes and (tid < RING) one ring node -> shared.
+  // One loop body, not unrolled, serves all, so the equation of state, the
   // exponentials and the reservoir path are emitted once.
 #pragma unroll 1
-  for (int w = 0; w < 2; ++w) {
-    if (w == 1 && tid >= SH::RING) break;
-    const uint8_t tw = w ? ring_t : own_t;
-    R r1 = w ? r1r : rho1, r2 = w ? r2r : rho2;
-    if (is_res(tw)) res_density<R, TF>(P, tw, step, tin, fin, N, w ? ring_idx : own_idx, theta, r1, r2);
+  for (int w = 0; w <= NPT; ++w) {
+    const bool ring = w == NPT;
+    if (ring && tid >= SH::RING) break;
+    const uint8_t tw = ring ? ring_t : pick(own_tv, w);
+    R r1 = ring ? r1r : pick(rho1v, w), r2 = ring ? r2r : pick(rho2v, w);
+    if (is_res(tw)) res_density<R, TF>(P, tw, step, tin, fin, N, ring ? ring_idx : pick(own_iv, w), theta, r1, r2);
     R ps = R(0), p1 = R(0), p2 = R(0);
     if (is_live(tw)) potentials<R>(P, r1, r2, ps, p1, p2, status);
     const bool mk = is_live(tw) && r1 > theta;
-    const int slot = w ? er : eo;
+    const int slot = ring ? er : (ty + 1 + w * SH::RY) * SH::EXT_X + (tx + 1);
     spot[slot] = Pot<R>{ps, p1, p2, code_bits<R>(node_code(tw, mk))};
     st_[slot] = tw;
     sm_[slot] = mk ? 1 : 0;
@@ -484,225 +533,248 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
   if (__syncthreads_or(waited_ok ? 0 : 1)) return true;
   after_sync();
 
-  R mymax = R(-1.0 / 0.0);
-  if (own && is_fluid(t)) {
-    mymax = rho1;
-    // ---- forces (Eqs. 11, 14a/b, 16) with mirror-image solid neighbours
-    // (force_stencils).
-    const Pot<R> pc = spot[eo];
-    const R psc = pc.ps, p1c = pc.p1, p2c = pc.p2;
-    // neighbour codes kept for the pushes: the low nibble of each of the eight
-    // neighbours (nbits, 4 bits per direction) and the raw-type pair of the four
-    // axis neighbours (abits, 2 bits per direction)
-    unsigned nbits = 0u, abits = 0u;
-    const int c0 = code_of<R>(pc.code);
-    R vps[9], vp1[9], vp2[9];
-    bool lv[9];
-    vps[0] = psc;
-    vp1[0] = p1c;
-    vp2[0] = p2c;
-    lv[0] = true;
-#pragma unroll
-    for (int a = 1; a < 9; ++a) {
-      const Pot<R> q = spot[eo + EY(a) * SH::EXT_X + EX(a)];
-      const int ca = code_of<R>(q.code);
-      nbits |= unsigned(ca & 0xF) << (4 * (a - 1));
-      if (a < 5) abits |= unsigned((ca >> 5) & 0x3) << (2 * (a - 1));
-      lv[a] = (ca & C_LIVE) != 0;
-      vps[a] = q.ps;
-      vp1[a] = q.p1;
-      vp2[a] = q.p2;
-    }
-    const Stencils<R> S = force_stencils<R>(vps, vp1, vp2, lv);
-    const R spx = S.psx, spy = S.psy, s2x = S.p2x, s2y = S.p2y, s1x = S.p1x, s1y = S.p1y, ssx = S.ssx,
-            ssy = S.ssy;
-    const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0],
-            w2 = rp<R>(P).w_adh[1];
-    const R F1x = force1<R>(G11, G12, w1, psc, p1c, spx, s2x, ssx, rho1, rp<R>(P).gx);
-    const R F1y = force1<R>(G11, G12, w1, psc, p1c, spy, s2y, ssy, rho1, rp<R>(P).gy);
-    const R F2x = force2<R>(G21, w2, p2c, s1x, ssx, rho2, rp<R>(P).gx);
-    const R F2y = force2<R>(G21, w2, p2c, s1y, ssy, rho2, rp<R>(P).gy);
-    // ---- velocities (Eqs. 17-19)
-    const R it1 = rp<R>(P).inv_tau[0], it2 = rp<R>(P).inv_tau[1];
-    const R rden = rrcp<R>(rfma<R>(rho1, it1, rmul<R>(rho2, it2)));
-    const R upx = u_common<R>(j1x, j2x, it1, it2, rden);
-    const R upy = u_common<R>(j1y, j2y, it1, it2, rden);
-    const R q1 = rho1 != R(0) ? rmul<R>(rp<R>(P).tau[0], rrcp<R>(rho1)) : R(0);
-    const R q2 = rho2 != R(0) ? rmul<R>(rp<R>(P).tau[1], rrcp<R>(rho2)) : R(0);
-    const R u1x = rfma<R>(F1x, q1, upx), u1y = rfma<R>(F1y, q1, upy);
-    const R u2x = rfma<R>(F2x, q2, upx), u2y = rfma<R>(F2y, q2, upy);
-    const R rrt = rrcp<R>(radd<R>(rho1, rho2));
-    const R urx = u_phys<R>(j1x, j2x, F1x, F2x, rrt);
-    const R ury = u_phys<R>(j1y, j2y, F1y, F2y, rrt);
-
-    const bool liq = (c0 & C_MARK) != 0;
-    tout[node] = liq ? T_LIQUID : T_GAS;
-
-    // neighbour indices for the push (constant offsets away from the edges)
-    int nb[9];
-#pragma unroll
-    for (int a = 1; a < 9; ++a) nb[a] = inner ? node + EX(a) + EY(a) * nx : nbr_index(P, x, y, EX(a), EY(a));
-
-    // ---- solutes: concentration with the Step-2 amendment, sources
-    if constexpr (Src::kReread) load_g();
-    R S1 = R(0), S2 = R(0);
-    R C[NS > 0 ? NS : 1];
-    R Sk[NS > 0 ? NS : 1];
-    if constexpr (NS > 0) {
-      if (liq) {
-        const bool appear = (t == T_GAS);
-        bool vnb = false;
-#pragma unroll
-        for (int b = 1; b < 5; ++b) {
-          // a neighbour that was liquid and is no longer marked liquid
-          vnb |= ((abits >> (2 * (b - 1))) & 1u) && !((nbits >> (4 * (b - 1))) & C_MARK);
-        }
-        if (appear || vnb) {
-          R dC[NS], cb[NS];
-          amend_marking<SH, R, TF, TG, NS>(P, tin, fin, gin, N, x, y, appear, st_, sm_, eo, theta, dC, cb);
-#pragma unroll
-          for (int k = 0; k < NS; ++k) {
-            const R J0 = rp<R>(P).J0[k], Ja = rp<R>(P).Ja[k];
-#pragma unroll
-            for (int a = 0; a < 5; ++a) {
-              const R ja = a == 0 ? J0 : Ja;
-              gs[k][a] = appear ? rfma<R>(ja, radd<R>(cb[k], dC[k]), -rmul<R>(ja, rp<R>(P).shift_c[k]))
-                                : rfma<R>(ja, dC[k], gs[k][a]);
-            }
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          R s = gs[k][0];
-#pragma unroll
-          for (int a = 1; a < 5; ++a) s += gs[k][a];
-          C[k] = rp<R>(P).shift_c[k] + s;
-        }
-        // homogeneous reactions (Eqs. 5a, 5c; sources Eqs. 27, 28)
-        R CA = R(0), CB = R(0), CE = R(0), tot = R(0);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          if (k == P.iA) CA = C[k];
-          if (k == P.iB) CB = C[k];
-          if (k == P.iE) CE = C[k];
-          tot += C[k];
-        }
-        if (P.iA == -2) CA = rmax<R>(R(0), rfma<R>(rp<R>(P).c_total_per_rho1, rho1, -tot));
-        // Section 2: R1 is faster at the surface of D(s) (a liquid node with a
-        // D(s) node on an axis link)
-        bool surf = false;
-        if (P.r1_surf) {
-#pragma unroll
-          for (int b = 1; b < 5; ++b) surf |= ((abits >> (2 * (b - 1) + 1)) & 1u) != 0;
-        }
-        R R1 = rmul<R>(surf ? rp<R>(P).k1_s : rp<R>(P).k1, CA);
-        if (P.has_rev)
-          R1 = rsub<R>(R1, rmul<R>(rmul<R>(surf ? rp<R>(P).k1_inv_Keq_s : rp<R>(P).k1_inv_Keq, CB),
-                                   rsqrt_<R>(rmax<R>(rmul<R>(rho2, rp<R>(P).inv_M_C), R(0)))));
-        const R R3 = rmul<R>(rmul<R>(rp<R>(P).k3, CB), CE);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) Sk[k] = rfma<R>(rp<R>(P).cR1[k], R1, rmul<R>(rp<R>(P).cR3[k], R3));
-        S1 = -rmul<R>(rp<R>(P).gas_yield, R1);
-        S2 = rmul<R>(rp<R>(P).gas_yield, R1);
-      }
-    }
-
-    // ---- fluid collision (Eq. 6, Eq. 8 at u_eq) and push streaming.  The
-    // collision runs relative to this node's shift; a value pushed into a node
-    // whose new phase has another shift is re-based by w (shift - shift').
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const R rho = s == 0 ? rho1 : rho2;
-      const R dr = s == 0 ? d1 : d2;
-      const R ux = s == 0 ? u1x : u2x, uy = s == 0 ? u1y : u2y;
-      const R itau = s == 0 ? it1 : it2;
-      const R Ssrc = s == 0 ? S1 : S2;
-      const R uu = half_u2<R>(ux, uy);
-      const R shs = s == 0 ? sh1 : sh2;
-      const R dl = shs - rp<R>(P).shift_f[s], dg = shs - rp<R>(P).shift_fg[s];
-      const R down = liq ? dl : dg;
-      if constexpr (Src::kReread) {
-        // the stage still holds this tile: read the component's populations
-        // again rather than keeping them in registers across the barrier
-        src.own_fc(own_idx, s, s == 0 ? f1 : f2);
-      }
-      TF* fo = fout + s * 9 * N;
-      // Eq. 8 relative to the node's shift, for opposite directions a, a'
-      // together: w (dr + rho (4.5 (e.u)^2 - 1.5 u^2)) +- 3 w rho e.u
-      R feq[9];
-      feq_pairs<R>(dr, rho, ux, uy, uu, feq);
+  // ---- phase 2, node by node
+#pragma unroll 1
+  for (int kn = 0; kn < NPT; ++kn) {
+    const int ly = ty + kn * SH::RY;
+    const int x = tl.x0 + tx, y = tl.y0 + ly;
+    const bool own = x < nx && y < P.ny;
+    const int node = y * nx + x;
+    const int eo = (ly + 1) * SH::EXT_X + (tx + 1);
+    const uint8_t own_t = pick(own_tv, kn);
+    const int own_idx = pick(own_iv, kn);
+    const uint8_t t = own ? own_t : T_WALL;
+    const R sh1 = fshift<R>(P, 0, own_t), sh2 = fshift<R>(P, 1, own_t);
+    const R rho1 = pick(rho1v, kn), rho2 = pick(rho2v, kn), d1 = pick(d1v, kn), d2 = pick(d2v, kn);
+    const R j1x = pick(j1xv, kn), j1y = pick(j1yv, kn), j2x = pick(j2xv, kn), j2y = pick(j2yv, kn);
+    R f1[9], f2[9];
+    if constexpr (kHold) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        const R fa = s == 0 ? f1[a] : f2[a];
-        const R w = w9<R>(a);
-        const R fs = bgk<R>(fa, feq[a], itau, w, Ssrc);
-        if (a == 0) {
-          st<TF, R>(fo + node, rfma<R>(w, down, fs));
-          continue;
-        }
-        // into a fluid neighbour (re-based to its new phase), or bounced back
-        // here from a solid or wall; nothing into a reservoir
-        const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
-        const bool fl = (c & C_FLUID) != 0;
-        const R sto = fl ? ((c & C_MARK) ? dl : dg) : down;
-        const int off = fl ? a * N + nb[a] : OPP(a) * N + node;
-        if (fl || !(c & C_RES)) st<TF, R>(fo + off, rfma<R>(w, sto, fs));
-        // a liquid node flags the minerals on its axis links for the VOP kernel
-        if (s == 0 && a < 5 && liq && (c & C_MIN))
-          atomicOr(&V.vmask[nb[a] >> 5], 1u << (nb[a] & 31));
+        f1[a] = q1[0][a];
+        f2[a] = q2[0][a];
       }
     }
+    R mymax = R(-1.0 / 0.0);
+    if (own && is_fluid(t)) {
+      mymax = rho1;
+      // ---- forces (Eqs. 11, 14a/b, 16) with mirror-image solid neighbours
+      // (force_stencils).
+      const Pot<R> pc = spot[eo];
+      const R psc = pc.ps, p1c = pc.p1, p2c = pc.p2;
+      // neighbour codes kept for the pushes: the low nibble of each of the eight
+      // neighbours (nbits, 4 bits per direction) and the raw-type pair of the four
+      // axis neighbours (abits, 2 bits per direction)
+      unsigned nbits = 0u, abits = 0u;
+      const int c0 = code_of<R>(pc.code);
+      R vps[9], vp1[9], vp2[9];
+      bool lv[9];
+      vps[0] = psc;
+      vp1[0] = p1c;
+      vp2[0] = p2c;
+      lv[0] = true;
+#pragma unroll
+      for (int a = 1; a < 9; ++a) {
+        const Pot<R> q = spot[eo + EY(a) * SH::EXT_X + EX(a)];
+        const int ca = code_of<R>(q.code);
+        nbits |= unsigned(ca & 0xF) << (4 * (a - 1));
+        if (a < 5) abits |= unsigned((ca >> 5) & 0x3) << (2 * (a - 1));
+        lv[a] = (ca & C_LIVE) != 0;
+        vps[a] = q.ps;
+        vp1[a] = q.p1;
+        vp2[a] = q.p2;
+      }
+      const Stencils<R> S = force_stencils<R>(vps, vp1, vp2, lv);
+      const R spx = S.psx, spy = S.psy, s2x = S.p2x, s2y = S.p2y, s1x = S.p1x, s1y = S.p1y, ssx = S.ssx,
+              ssy = S.ssy;
+      const R G11 = rp<R>(P).G11, G12 = rp<R>(P).G12, G21 = rp<R>(P).G21, w1 = rp<R>(P).w_adh[0],
+              w2 = rp<R>(P).w_adh[1];
+      const R F1x = force1<R>(G11, G12, w1, psc, p1c, spx, s2x, ssx, rho1, rp<R>(P).gx);
+      const R F1y = force1<R>(G11, G12, w1, psc, p1c, spy, s2y, ssy, rho1, rp<R>(P).gy);
+      const R F2x = force2<R>(G21, w2, p2c, s1x, ssx, rho2, rp<R>(P).gx);
+      const R F2y = force2<R>(G21, w2, p2c, s1y, ssy, rho2, rp<R>(P).gy);
+      // ---- velocities (Eqs. 17-19)
+      const R it1 = rp<R>(P).inv_tau[0], it2 = rp<R>(P).inv_tau[1];
+      const R rden = rrcp<R>(rfma<R>(rho1, it1, rmul<R>(rho2, it2)));
+      const R upx = u_common<R>(j1x, j2x, it1, it2, rden);
+      const R upy = u_common<R>(j1y, j2y, it1, it2, rden);
+      const R q1 = rho1 != R(0) ? rmul<R>(rp<R>(P).tau[0], rrcp<R>(rho1)) : R(0);
+      const R q2 = rho2 != R(0) ? rmul<R>(rp<R>(P).tau[1], rrcp<R>(rho2)) : R(0);
+      const R u1x = rfma<R>(F1x, q1, upx), u1y = rfma<R>(F1y, q1, upy);
+      const R u2x = rfma<R>(F2x, q2, upx), u2y = rfma<R>(F2y, q2, upy);
+      const R rrt = rrcp<R>(radd<R>(rho1, rho2));
+      const R urx = u_phys<R>(j1x, j2x, F1x, F2x, rrt);
+      const R ury = u_phys<R>(j1y, j2y, F1y, F2y, rrt);
 
-    // ---- solute collision (Eqs. 20-22 with u_r) and push streaming
-    if constexpr (NS > 0) {
-      if (liq) {
-        // Eq. 21 relative to the species' shift, opposite directions together:
-        // J_a (C - shift) +- C e.u / 2
-        R geq[NS][5];
+      const bool liq = (c0 & C_MARK) != 0;
+      tout[node] = liq ? T_LIQUID : T_GAS;
+
+      // neighbour indices for the push (constant offsets away from the edges)
+      int nb[9];
 #pragma unroll
-        for (int k = 0; k < NS; ++k) geq_pairs<R>(rp<R>(P).J0[k], rp<R>(P).Ja[k], C[k], rp<R>(P).shift_c[k], urx, ury,
-                                                  geq[k]);
+      for (int a = 1; a < 9; ++a) nb[a] = inner ? node + EX(a) + EY(a) * nx : nbr_index(P, x, y, EX(a), EY(a));
+
+      // ---- solutes: concentration with the Step-2 amendment, sources
+      if constexpr (!kHold) load_g(own, own_t, node);
+      R S1 = R(0), S2 = R(0);
+      R C[NS > 0 ? NS : 1];
+      R Sk[NS > 0 ? NS : 1];
+      if constexpr (NS > 0) {
+        if (liq) {
+          const bool appear = (t == T_GAS);
+          bool vnb = false;
 #pragma unroll
-        for (int a = 0; a < 5; ++a) {
-          // the rest population stays; a moving one goes into a liquid
-          // neighbour, out into a liquid reservoir, or bounces back here
-          // (no-flux / mineral link)
-          int dst = node, slot = a;
-          bool keep = true;
-          if (a > 0) {
-            const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
-            const bool into = (c & (C_FLUID | C_MARK)) == (C_FLUID | C_MARK);
-            const bool out = (c & (C_RES | C_MARK)) == (C_RES | C_MARK);
-            dst = into ? nb[a] : node;
-            slot = (into || out) ? a : OPP(a);
-            keep = !out;
+          for (int b = 1; b < 5; ++b) {
+            // a neighbour that was liquid and is no longer marked liquid
+            vnb |= ((abits >> (2 * (b - 1))) & 1u) && !((nbits >> (4 * (b - 1))) & C_MARK);
+          }
+          if (appear || vnb) {
+            R dC[NS], cb[NS];
+            amend_marking<SH, R, TF, TG, NS>(P, tin, fin, gin, N, x, y, appear, st_, sm_, eo, theta, dC, cb);
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+              const R J0 = rp<R>(P).J0[k], Ja = rp<R>(P).Ja[k];
+#pragma unroll
+              for (int a = 0; a < 5; ++a) {
+                const R ja = a == 0 ? J0 : Ja;
+                gs[k][a] = appear ? rfma<R>(ja, radd<R>(cb[k], dC[k]), -rmul<R>(ja, rp<R>(P).shift_c[k]))
+                                  : rfma<R>(ja, dC[k], gs[k][a]);
+              }
+            }
           }
 #pragma unroll
           for (int k = 0; k < NS; ++k) {
-            const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
-            const R gs_ = bgk<R>(gs[k][a], geq[k][a], rp<R>(P).inv_tau_g[k], ja, Sk[k]);
-            if (keep) gst<TG, R>(P, k, gout + (k * 5 + slot) * N + dst, gs_);
+            R s = gs[k][0];
+#pragma unroll
+            for (int a = 1; a < 5; ++a) s += gs[k][a];
+            C[k] = rp<R>(P).shift_c[k] + s;
           }
-        }
-      } else {
-        // gas node: no solute
+          // homogeneous reactions (Eqs. 5a, 5c; sources Eqs. 27, 28)
+          R CA = R(0), CB = R(0), CE = R(0), tot = R(0);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) {
+          for (int k = 0; k < NS; ++k) {
+            if (k == P.iA) CA = C[k];
+            if (k == P.iB) CB = C[k];
+            if (k == P.iE) CE = C[k];
+            tot += C[k];
+          }
+          if (P.iA == -2) CA = rmax<R>(R(0), rfma<R>(rp<R>(P).c_total_per_rho1, rho1, -tot));
+          // Section 2: R1 is faster at the surface of D(s) (a liquid node with a
+          // D(s) node on an axis link)
+          bool surf = false;
+          if (P.r1_surf) {
 #pragma unroll
-          for (int a = 0; a < 5; ++a)
-            gst<TG, R>(P, k, gout + (k * 5 + a) * N + node,
-                       -(a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k]) * rp<R>(P).shift_c[k]);
+            for (int b = 1; b < 5; ++b) surf |= ((abits >> (2 * (b - 1) + 1)) & 1u) != 0;
+          }
+          R R1 = rmul<R>(surf ? rp<R>(P).k1_s : rp<R>(P).k1, CA);
+          if (P.has_rev)
+            R1 = rsub<R>(R1, rmul<R>(rmul<R>(surf ? rp<R>(P).k1_inv_Keq_s : rp<R>(P).k1_inv_Keq, CB),
+                                     rsqrt_<R>(rmax<R>(rmul<R>(rho2, rp<R>(P).inv_M_C), R(0)))));
+          const R R3 = rmul<R>(rmul<R>(rp<R>(P).k3, CB), CE);
+#pragma unroll
+          for (int k = 0; k < NS; ++k) Sk[k] = rfma<R>(rp<R>(P).cR1[k], R1, rmul<R>(rp<R>(P).cR3[k], R3));
+          S1 = -rmul<R>(rp<R>(P).gas_yield, R1);
+          S2 = rmul<R>(rp<R>(P).gas_yield, R1);
         }
       }
-    }
-  } else if (own) {
-    if (is_res(t))
-      reservoir_push<SH, R, TF, TG, NS>(P, tin, fin, gin, fout, gout, N, x, y, t, step, theta, st_, sm_, eo);
-    tout[node] = t;
-  }
 
-  // ---- max of rho_1 over fluid nodes (next step's threshold) and status
-  acc.mx = rmax<R>(acc.mx, mymax);
+      // ---- fluid collision (Eq. 6, Eq. 8 at u_eq) and push streaming.  The
+      // collision runs relative to this node's shift; a value pushed into a node
+      // whose new phase has another shift is re-based by w (shift - shift').
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const R rho = s == 0 ? rho1 : rho2;
+        const R dr = s == 0 ? d1 : d2;
+        const R ux = s == 0 ? u1x : u2x, uy = s == 0 ? u1y : u2y;
+        const R itau = s == 0 ? it1 : it2;
+        const R Ssrc = s == 0 ? S1 : S2;
+        const R uu = half_u2<R>(ux, uy);
+        const R shs = s == 0 ? sh1 : sh2;
+        const R dl = shs - rp<R>(P).shift_f[s], dg = shs - rp<R>(P).shift_fg[s];
+        const R down = liq ? dl : dg;
+        if constexpr (!kHold) {
+          // read the component's populations again (from the stage, or from L1)
+          // rather than keeping them in registers across the barrier
+          src.own_fc(own_idx, ly, s, s == 0 ? f1 : f2);
+        }
+        TF* fo = fout + s * 9 * N;
+        // Eq. 8 relative to the node's shift, for opposite directions a, a'
+        // together: w (dr + rho (4.5 (e.u)^2 - 1.5 u^2)) +- 3 w rho e.u
+        R feq[9];
+        feq_pairs<R>(dr, rho, ux, uy, uu, feq);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+          const R fa = s == 0 ? f1[a] : f2[a];
+          const R w = w9<R>(a);
+          const R fs = bgk<R>(fa, feq[a], itau, w, Ssrc);
+          if (a == 0) {
+            st<TF, R>(fo + node, rfma<R>(w, down, fs));
+            continue;
+          }
+          // into a fluid neighbour (re-based to its new phase), or bounced back
+          // here from a solid or wall; nothing into a reservoir
+          const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
+          const bool fl = (c & C_FLUID) != 0;
+          const R sto = fl ? ((c & C_MARK) ? dl : dg) : down;
+          const int off = fl ? a * N + nb[a] : OPP(a) * N + node;
+          if (fl || !(c & C_RES)) st<TF, R>(fo + off, rfma<R>(w, sto, fs));
+          // a liquid node flags the minerals on its axis links for the VOP kernel
+          if (s == 0 && a < 5 && liq && (c & C_MIN))
+            atomicOr(&V.vmask[nb[a] >> 5], 1u << (nb[a] & 31));
+        }
+      }
+
+      // ---- solute collision (Eqs. 20-22 with u_r) and push streaming
+      if constexpr (NS > 0) {
+        if (liq) {
+          // Eq. 21 relative to the species' shift, opposite directions together:
+          // J_a (C - shift) +- C e.u / 2
+          R geq[NS][5];
+#pragma unroll
+          for (int k = 0; k < NS; ++k) geq_pairs<R>(rp<R>(P).J0[k], rp<R>(P).Ja[k], C[k], rp<R>(P).shift_c[k], urx, ury,
+                                                    geq[k]);
+#pragma unroll
+          for (int a = 0; a < 5; ++a) {
+            // the rest population stays; a moving one goes into a liquid
+            // neighbour, out into a liquid reservoir, or bounces back here
+            // (no-flux / mineral link)
+            int dst = node, slot = a;
+            bool keep = true;
+            if (a > 0) {
+              const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
+              const bool into = (c & (C_FLUID | C_MARK)) == (C_FLUID | C_MARK);
+              const bool out = (c & (C_RES | C_MARK)) == (C_RES | C_MARK);
+              dst = into ? nb[a] : node;
+              slot = (into || out) ? a : OPP(a);
+              keep = !out;
+            }
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+              const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
+              const R gs_ = bgk<R>(gs[k][a], geq[k][a], rp<R>(P).inv_tau_g[k], ja, Sk[k]);
+              if (keep) gst<TG, R>(P, k, gout + (k * 5 + slot) * N + dst, gs_);
+            }
+          }
+        } else {
+          // gas node: no solute
+#pragma unroll
+          for (int k = 0; k < NS; ++k) {
+#pragma unroll
+            for (int a = 0; a < 5; ++a)
+              gst<TG, R>(P, k, gout + (k * 5 + a) * N + node,
+                         -(a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k]) * rp<R>(P).shift_c[k]);
+          }
+        }
+      }
+    } else if (own) {
+      if (is_res(t))
+        reservoir_push<SH, R, TF, TG, NS>(P, tin, fin, gin, fout, gout, N, x, y, t, step, theta, st_, sm_, eo);
+      tout[node] = t;
+    }
+
+    // ---- max of rho_1 over fluid nodes (next step's threshold)
+    acc.mx = rmax<R>(acc.mx, mymax);
+  }
   acc.status |= status;
   return false;
 }
@@ -717,14 +789,14 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
 // view and step limit are read, and the accumulators flushed, once per run of
 // consecutive tiles of one instance.
 template <class SH, class TF, class TG, class R, int NS, bool SINGLE>
-__global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const Tile* __restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R, SH::NPT>()) k_bulk(const Tile* __restrict__ tiles, int ntiles,
                                                                          const DevInst* __restrict__ insts) {
   __shared__ Pot<R> s_pot[2][SH::EXT];
   __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
   const int stride = gridDim.x;
   TileAcc<R> acc{R(-1.0 / 0.0), 0u};
   int buf = 0;
-  TileTypes tt;
+  TileTypes<SH::NPT> tt;
   if constexpr (SINGLE) {
     // one simulation: all tiles are live or none is
     if (!(insts->scal[S_STEP] < insts->scal[S_LIMIT])) return;
@@ -737,7 +809,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
     while (ti < ntiles) {
       const int nt = ti + stride;
       const Tile tn = nt < ntiles ? tiles[nt] : Tile{};
-      auto next_types = [&](TileTypes& t) {
+      auto next_types = [&](TileTypes<SH::NPT>& t) {
         if (nt < ntiles) t = load_types<SH>(tn, P, V.tin, threadIdx.x);
       };
       bulk_tile<SH, TF, TG, R, NS>(tl, V, P, src, [] {}, next_types, true, tt, acc, s_pot[buf], s_t[buf],
@@ -773,7 +845,7 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
         const DevParams& P = insts[vinst].P;
         if (!have_tt) tt = load_types<SH>(tl, P, V.tin, threadIdx.x);
         const bool same = nt < ntiles && tn.inst == vinst;
-        auto next_types = [&](TileTypes& t) {
+        auto next_types = [&](TileTypes<SH::NPT>& t) {
           if (same) t = load_types<SH>(tn, P, V.tin, threadIdx.x);
         };
         const GlobalSrc<TF, TG, R, NS> src{V.fin, V.gin, V.N};
@@ -798,7 +870,8 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R>()) k_bulk(const T
 // then plane).
 template <class SH, class TG, int NS, bool STAGE_G = true>
 struct StageCfg {
-  static constexpr int BX = SH::TX + 2 * STAGE_HALO_X, BY = SH::TY + 2;
+  static constexpr int HX = stage_halo_x(SH::NPT);
+  static constexpr int BX = SH::TX + 2 * HX, BY = SH::TY + 2;
   static constexpr int FBYTES = BX * BY * 18 * 4;
   static constexpr int GBYTES = (NS > 0 && STAGE_G) ? SH::TX * SH::TY * 5 * NS * (int)sizeof(TG) : 0;
   static constexpr int FOFF = 0;
@@ -821,12 +894,14 @@ struct StageSrc {
   const TG* gs_;       // stage D2Q5 box (STAGE_G) or the solute populations in global memory
   const float* fin;
   int N, nx, ny, x0, y0;
+  static_assert(!STAGE_G || SH::NPT == 1, "the staged D2Q5 box is indexed by thread");
   // A thread position beyond the lattice edge of a partial tile stands for the
   // wrapped node across a periodic edge (idx >= 0 only then): not in the box.
-  __device__ __forceinline__ void own_f(int idx, float* f1, float* f2) const {
-    const int tx = threadIdx.x % SH::TX, ty = threadIdx.x / SH::TX;
-    if (x0 + tx < nx && y0 + ty < ny) {
-      const float* b = fs + (ty + 1) * C::BX + (tx + STAGE_HALO_X);
+  // ly: the node's row in the tile.
+  __device__ __forceinline__ void own_f(int idx, int ly, float* f1, float* f2) const {
+    const int tx = threadIdx.x % SH::TX;
+    if (x0 + tx < nx && y0 + ly < ny) {
+      const float* b = fs + (ly + 1) * C::BX + (tx + C::HX);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         f1[a] = b[a * C::BX * C::BY];
@@ -841,10 +916,10 @@ struct StageSrc {
     }
   }
   // one component's populations (as own_f)
-  __device__ __forceinline__ void own_fc(int idx, int comp, float* f) const {
-    const int tx = threadIdx.x % SH::TX, ty = threadIdx.x / SH::TX;
-    if (x0 + tx < nx && y0 + ty < ny) {
-      const float* b = fs + (ty + 1) * C::BX + (tx + STAGE_HALO_X) + comp * 9 * C::BX * C::BY;
+  __device__ __forceinline__ void own_fc(int idx, int ly, int comp, float* f) const {
+    const int tx = threadIdx.x % SH::TX;
+    if (x0 + tx < nx && y0 + ly < ny) {
+      const float* b = fs + (ly + 1) * C::BX + (tx + C::HX) + comp * 9 * C::BX * C::BY;
 #pragma unroll
       for (int a = 0; a < 9; ++a) f[a] = b[a * C::BX * C::BY];
     } else {
@@ -866,9 +941,13 @@ struct StageSrc {
         for (int a = 0; a < 5; ++a) g[k][a] = ld<float>(gs_ + (k * 5 + a) * N + node);
     }
   }
+  // a ring node inside the lattice and the box: from the box; otherwise
+  // (across a periodic edge, or a side column of a box without x halo) from
+  // global memory
   __device__ __forceinline__ void ring_density(int ring_idx, int rx, int ry, float& d1, float& d2) const {
-    if (rx >= 0 && rx < nx && ry >= 0 && ry < ny) {
-      const float* b = fs + (ry - y0 + 1) * C::BX + (rx - x0 + STAGE_HALO_X);
+    const bool in_box = C::HX > 0 || (rx >= x0 && rx < x0 + SH::TX);
+    if (rx >= 0 && rx < nx && ry >= 0 && ry < ny && in_box) {
+      const float* b = fs + (ry - y0 + 1) * C::BX + (rx - x0 + C::HX);
       float s1 = b[0], s2 = b[9 * C::BX * C::BY];
 #pragma unroll
       for (int a = 1; a < 9; ++a) {
@@ -891,7 +970,7 @@ __device__ __forceinline__ void stage_issue(const Tile& d, const CUtensorMap* mf
                                             unsigned char* stage, uint64_t* bar) {
   using C = StageCfg<SH, TG, NS, STAGE_G>;
   mbar_arrive_expect_tx(bar, C::TX_BYTES);
-  tma_load_3d(stage + C::FOFF, mf, bar, d.x0 - STAGE_HALO_X, d.y0 - 1, 0);
+  tma_load_3d(stage + C::FOFF, mf, bar, d.x0 - C::HX, d.y0 - 1, 0);
   if constexpr (NS > 0 && STAGE_G) tma_load_3d(stage + C::GOFF, mg, bar, d.x0, d.y0, 0);
 }
 
@@ -926,8 +1005,15 @@ constexpr int tma_smem() {
   return 2 * StageCfg<SH, TG, NS, MODE == 1>::STAGE;
 }
 
+// Resident blocks per SM of a staged variant: MODE 1 two; MODE 2 three with
+// one node per thread, two with two (a larger box, more registers).
+template <class SH, int MODE>
+constexpr int tma_min_blocks() {
+  return (MODE == 1 || SH::NPT > 1) ? 2 : 3;
+}
+
 template <class SH, int SHAPE, class TG, int NS, int MODE, bool SINGLE>
-__global__ void __launch_bounds__(NTHREADS, MODE == 1 ? 2 : 3)
+__global__ void __launch_bounds__(NTHREADS, tma_min_blocks<SH, MODE>())
     k_bulk_tma(const Tile* __restrict__ tiles, int ntiles, const DevInst* __restrict__ insts,
                const __grid_constant__ DevParams Pk) {
   constexpr bool SG = MODE == 1;   // solute box staged too
@@ -982,7 +1068,7 @@ __global__ void __launch_bounds__(NTHREADS, MODE == 1 ? 2 : 3)
     if (ti < ntiles) issue(d0, dyn, &bars[0]);
     if (t1 < ntiles) issue(d1, dyn + C::STAGE, &bars[1]);
   }
-  TileTypes tt;
+  TileTypes<SH::NPT> tt;
   bool have_tt = false;             // tt holds the current tile's types
   int vinst = SINGLE ? 0 : -1;      // instance of the run in progress (batch)
   bool vlive = SINGLE;              // ... below its step limit
@@ -1024,7 +1110,7 @@ __global__ void __launch_bounds__(NTHREADS, MODE == 1 ? 2 : 3)
       const DevParams& P = SINGLE ? Pk : insts[vinst].P;
       if (!have_tt) tt = load_types<SH>(d0, P, V.tin, threadIdx.x);
       const bool same = t1 < ntiles && (SINGLE || d1.inst == vinst);
-      auto next_types = [&](TileTypes& t) {
+      auto next_types = [&](TileTypes<SH::NPT>& t) {
         if (same) t = load_types<SH>(d1, P, V.tin, threadIdx.x);
       };
       const StageSrc<SH, TG, NS, SG> src{(const float*)(stage + C::FOFF),

@@ -16,30 +16,39 @@ constexpr uint8_t T_MASK = 0x0F;     // low nibble: node type
 constexpr uint8_t T_NEW = 0x40;      // flag set by the amendment kernel: solid -> liquid this step
 constexpr uint8_t T_VANISH = 0x80;   // flag: liquid -> solid this step
 
-// Tile shapes of the step kernels: 256 threads, one per interior node, and a
-// one-node ring.  The runtime picks the faster shape per handle or batch by
-// timing its first steps (results do not depend on the shape).
+// Tile shapes of the step kernels: 256 threads, a tile of TX x TY nodes and a
+// one-node ring.  Thread (tx, ty) of a TX x RY block computes the NPT nodes
+// (tx, ty + k RY) of the tile, k < NPT (nodes per thread).  The runtime picks
+// the fastest shape per handle or batch by timing its first steps (results do
+// not depend on the shape).
 constexpr int NTHREADS = 256;
 // Interface-bitmap words per warp chunk of the VOP kernel.
 constexpr int VOP_CHUNK = 4;
-template <int TX_, int TY_>
+template <int TX_, int RY_, int NPT_ = 1>
 struct TileShape {
-  static constexpr int TX = TX_, TY = TY_;
+  static constexpr int TX = TX_, RY = RY_, NPT = NPT_, TY = RY_ * NPT_;
   static constexpr int EXT_X = TX + 2, EXT_Y = TY + 2;
   static constexpr int EXT = EXT_X * EXT_Y;
   static constexpr int RING = EXT - TX * TY;
-  static_assert(TX * TY == NTHREADS, "one thread per interior node");
+  static_assert(TX * RY == NTHREADS, "one thread per column position and row of a pass");
   static_assert(RING <= NTHREADS, "one ring node per thread");
 };
-using ShapeA = TileShape<16, 16>;
-using ShapeB = TileShape<32, 8>;
-constexpr int NSHAPES = 2;
-constexpr int SHAPE_TX[NSHAPES] = {ShapeA::TX, ShapeB::TX};
-constexpr int SHAPE_TY[NSHAPES] = {ShapeA::TY, ShapeB::TY};
+using ShapeA = TileShape<16, 16>;      // 16 x 16, one node per thread
+using ShapeB = TileShape<32, 8>;       // 32 x 8, one node per thread
+using ShapeC = TileShape<16, 16, 2>;   // 16 x 32, two nodes per thread
+using ShapeD = TileShape<32, 8, 2>;    // 32 x 16, two nodes per thread
+constexpr int NSHAPES = 4;
+constexpr int SHAPE_TX[NSHAPES] = {ShapeA::TX, ShapeB::TX, ShapeC::TX, ShapeD::TX};
+constexpr int SHAPE_TY[NSHAPES] = {ShapeA::TY, ShapeB::TY, ShapeC::TY, ShapeD::TY};
+constexpr int SHAPE_NPT[NSHAPES] = {ShapeA::NPT, ShapeB::NPT, ShapeC::NPT, ShapeD::NPT};
 // The staged bulk kernel's D2Q9 box reaches this many nodes left and right of
-// its tile (one ring node is needed; four keep the box's x origin on a 16-byte
-// boundary for FP32 rows), and one node above and below.
+// a tile of one node per thread (one ring node is needed; four keep the box's
+// x origin on a 16-byte boundary for FP32 rows), and one node above and below.
+// The box of a tile of two nodes per thread has no x halo (the tile's own x
+// origin is aligned; its side ring columns are read from global memory), so
+// that two blocks with two stages each fit on an SM.
 constexpr int STAGE_HALO_X = 4;
+__host__ __device__ constexpr int stage_halo_x(int npt) { return npt == 1 ? STAGE_HALO_X : 0; }
 
 // Per-instance scalar slots (unsigned long long each).
 enum {

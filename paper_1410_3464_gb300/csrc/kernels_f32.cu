@@ -3,4 +3,5 @@
 #define KTG float
 #define KR float
 #define KNAME launchers_f32
+#define KPART 1
 #include "kernels_impl.cuh"

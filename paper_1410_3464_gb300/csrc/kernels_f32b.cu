@@ -3,4 +3,5 @@
 #define KTG __nv_bfloat16
 #define KR float
 #define KNAME launchers_f32b
+#define KPART 1
 #include "kernels_impl.cuh"

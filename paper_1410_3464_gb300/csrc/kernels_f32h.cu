@@ -3,4 +3,5 @@
 #define KTG __half
 #define KR float
 #define KNAME launchers_f32h
+#define KPART 1
 #include "kernels_impl.cuh"

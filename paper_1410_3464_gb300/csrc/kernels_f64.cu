@@ -3,4 +3,5 @@
 #define KTG double
 #define KR double
 #define KNAME launchers_f64
+#define KPART 1
 #include "kernels_impl.cuh"

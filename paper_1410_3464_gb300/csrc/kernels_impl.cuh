@@ -1,6 +1,9 @@
 // Explicit instantiation of the step kernels for one storage precision.
-// Included by one translation unit per precision with KTF (population
-// storage), KTG (solute storage), KR (compute type) and KNAME defined.
+// Included by two translation units per precision with KTF (population
+// storage), KTG (solute storage), KR (compute type), KNAME and KPART defined:
+// KPART 1 holds the tile shapes of one node per thread and every other
+// kernel, KPART 2 the bulk kernels of two nodes per thread (compiled apart so
+// that the units build in parallel); the runtime merges the two tables.
 #include "launch.h"
 #include "bulk.cuh"
 #include "interface.cuh"
@@ -32,9 +35,9 @@ void bulk_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* insts,
   else
     k_bulk<SH, KTF, KTG, KR, NS, false><<<bulk_grid<SH, NS, false>(ntiles), NTHREADS, 0, s>>>(tiles, ntiles, insts);
 }
-// Staged variants: grid of as many blocks as fit (two per SM with the
-// double-buffered stage, three with the single stage), dynamic shared memory
-// opted in once.
+// Staged variants: grid of as many blocks as fit (two or three per SM, by
+// the variant's shared memory and registers), dynamic shared memory opted in
+// once.
 template <class SH, int SHAPE, int NS, int MODE, bool SINGLE>
 int bulk_tma_cap() {
   constexpr int smem = tma_smem<SH, KTG, NS, MODE>();
@@ -67,6 +70,7 @@ void bulk_tma_l(cudaStream_t s, const Tile* tiles, int ntiles, const DevInst* in
         <<<ntiles < cap ? ntiles : cap, NTHREADS, smem, s>>>(tiles, ntiles, insts, unused);
   }
 }
+#if KPART == 1
 // Grid over the chunks of VOP_CHUNK interface-bitmap words of all members
 // (one chunk per warp), capped at one wave of resident blocks (warps then
 // stride).
@@ -108,20 +112,37 @@ void budget_l(cudaStream_t s, const DevInst* I, double* part, double* out) {
   k_budget_partial<KTF, KTG, KR, NS><<<BUD_BLOCKS, BUD_THREADS, 0, s>>>(I, part);
   k_budget_final<<<1, BUD_FINAL_THREADS, 0, s>>>(part, BUD_BLOCKS, out);
 }
+#endif
 
 template <int NS>
 constexpr Launchers make() {
+#if KPART == 1
   if constexpr (sizeof(KTF) == 4) {
-    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>},
-                     {&bulk_tma_l<ShapeA, 0, NS, 1>, &bulk_tma_l<ShapeB, 1, NS, 1>},
-                     {&bulk_tma_l<ShapeA, 0, NS, 2>, &bulk_tma_l<ShapeB, 1, NS, 2>},
+    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>, nullptr, nullptr},
+                     {&bulk_tma_l<ShapeA, 0, NS, 1>, &bulk_tma_l<ShapeB, 1, NS, 1>, nullptr, nullptr},
+                     {&bulk_tma_l<ShapeA, 0, NS, 2>, &bulk_tma_l<ShapeB, 1, NS, 2>, nullptr, nullptr},
                      &vop_l<NS>,
                      &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
   } else {
-    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>}, {nullptr, nullptr}, {nullptr, nullptr},
+    return Launchers{{&bulk_l<ShapeA, NS>, &bulk_l<ShapeB, NS>, nullptr, nullptr},
+                     {nullptr, nullptr, nullptr, nullptr},
+                     {nullptr, nullptr, nullptr, nullptr},
                      &vop_l<NS>,
                      &amend_l<NS>, &init_l<NS>, &fields_l<NS>, &budget_l<NS>};
   }
+#else
+  if constexpr (sizeof(KTF) == 4) {
+    return Launchers{{nullptr, nullptr, &bulk_l<ShapeC, NS>, &bulk_l<ShapeD, NS>},
+                     {nullptr, nullptr, nullptr, nullptr},
+                     {nullptr, nullptr, &bulk_tma_l<ShapeC, 2, NS, 2>, &bulk_tma_l<ShapeD, 3, NS, 2>},
+                     nullptr, nullptr, nullptr, nullptr, nullptr};
+  } else {
+    return Launchers{{nullptr, nullptr, &bulk_l<ShapeC, NS>, &bulk_l<ShapeD, NS>},
+                     {nullptr, nullptr, nullptr, nullptr},
+                     {nullptr, nullptr, nullptr, nullptr},
+                     nullptr, nullptr, nullptr, nullptr, nullptr};
+  }
+#endif
 }
 const Launchers table[MAXS + 1] = {make<0>(), make<1>(), make<2>(), make<3>(), make<4>()};
 

@@ -462,8 +462,15 @@ __global__ void k_batch_monitor(const DevInst* __restrict__ insts, int n, unsign
   }
 }
 
+// Whether the bulk kernel of a variant is compiled (the staged kernels exist
+// for the shapes of one node per thread).
+bool variant_exists(const Stepper& st, int sh, int sg) {
+  return sg == 0 ? st.L->bulk[sh] != nullptr : sg == 1 ? st.L->bulk_tma[sh] != nullptr : st.L->bulk_tma1[sh] != nullptr;
+}
+
 // Variants the stepper may use: every tile shape and staging the caller left
-// open (staging only where every instance has TMA descriptors).
+// open (staging only where every instance has TMA descriptors and the shape
+// has a staged kernel).
 std::vector<std::pair<int, int>> candidates(const Stepper& st) {
   std::vector<std::pair<int, int>> c;
   for (int sh = 0; sh < NSHAPES; ++sh) {
@@ -471,6 +478,7 @@ std::vector<std::pair<int, int>> candidates(const Stepper& st) {
     for (int sg = 0; sg < NSTAGING; ++sg) {
       if (st.fix_staged >= 0 && sg != st.fix_staged) continue;
       if (sg >= 1 && !st.staged_ok) continue;
+      if (!variant_exists(st, sh, sg)) continue;
       c.push_back({sh, sg});
     }
   }
@@ -603,7 +611,13 @@ pslbm_status set_shape(Stepper& st, int tx, int ty) {
   for (int sh = 0; sh < NSHAPES; ++sh)
     if (SHAPE_TX[sh] == tx && SHAPE_TY[sh] == ty) idx = sh;
   if (idx == -2) return PSLBM_ERR_PARAM;
+  const int prev = st.fix_shape;
   st.fix_shape = idx;
+  if (candidates(st).empty()) {
+    // a fixed staging that this shape has no kernel for
+    st.fix_shape = prev;
+    return PSLBM_ERR_PARAM;
+  }
   choose(st);
   return PSLBM_OK;
 }
@@ -612,7 +626,13 @@ pslbm_status set_shape(Stepper& st, int tx, int ty) {
 // 2: TMA-staged with a single stage).
 pslbm_status set_staging(Stepper& st, int mode) {
   if (mode < -1 || mode >= NSTAGING || (mode >= 1 && !st.staged_ok)) return PSLBM_ERR_PARAM;
+  const int prev = st.fix_staged;
   st.fix_staged = mode;
+  if (candidates(st).empty()) {
+    // a fixed tile shape that has no kernel of this staging
+    st.fix_staged = prev;
+    return PSLBM_ERR_PARAM;
+  }
   choose(st);
   return PSLBM_OK;
 }
@@ -655,7 +675,8 @@ bool encode_maps(DevInst& I, const pslbm_params* p) {
     for (int b = 0; b < 2; ++b) {
       const cuuint64_t fdim[3] = {nx, ny, 18};
       const cuuint64_t fstr[2] = {nx * 4, N * 4};
-      const cuuint32_t fbox[3] = {(cuuint32_t)(SHAPE_TX[sh] + 2 * STAGE_HALO_X), (cuuint32_t)(SHAPE_TY[sh] + 2), 18};
+      const cuuint32_t fbox[3] = {(cuuint32_t)(SHAPE_TX[sh] + 2 * stage_halo_x(SHAPE_NPT[sh])),
+                                  (cuuint32_t)(SHAPE_TY[sh] + 2), 18};
       const cuuint32_t one[3] = {1, 1, 1};
       if (enc(&I.tmf[sh][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, I.f[b], fdim, fstr, fbox, one,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -917,7 +938,8 @@ pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes)
 pslbm_status pslbm_set_tile_shape(pslbm_t h, int32_t tile_x, int32_t tile_y) {
   if (!h) return fail(nullptr, PSLBM_ERR_PARAM, "handle is NULL");
   if (set_shape(h->run, tile_x, tile_y) != PSLBM_OK)
-    return fail(h, PSLBM_ERR_PARAM, "unsupported tile shape (0x0, 16x16 or 32x8)");
+    return fail(h, PSLBM_ERR_PARAM,
+                "unsupported tile shape (0x0, 16x16, 32x8, 16x32 or 32x16; the last two have no staged kernel)");
   return PSLBM_OK;
 }
 
@@ -1095,9 +1117,11 @@ pslbm_status pslbm_batch_create(int32_t n, const pslbm_t* members, int32_t tile_
   if (!b) return fail(nullptr, PSLBM_ERR_OOM, "host allocation failed");
   b->run.staged_ok = true;
   for (int i = 0; i < n; ++i) b->run.staged_ok = b->run.staged_ok && members[i]->run.staged_ok;
+  b->L = members[0]->L;
+  b->run.L = b->L;
   if (set_shape(b->run, tile_x, tile_y) != PSLBM_OK) {
     delete b;
-    return fail(nullptr, PSLBM_ERR_PARAM, "unsupported tile shape (0x0, 16x16 or 32x8)");
+    return fail(nullptr, PSLBM_ERR_PARAM, "unsupported tile shape (0x0, 16x16, 32x8, 16x32 or 32x16)");
   }
   std::vector<DevInst> di;
   for (int i = 0; i < n; ++i) {
@@ -1249,13 +1273,40 @@ const Launchers* launchers_f64(int ns);
 const Launchers* launchers_f32(int ns);
 const Launchers* launchers_f32h(int ns);
 const Launchers* launchers_f32b(int ns);
+const Launchers* launchers_f64_n2(int ns);
+const Launchers* launchers_f32_n2(int ns);
+const Launchers* launchers_f32h_n2(int ns);
+const Launchers* launchers_f32b_n2(int ns);
+
+// The two halves of a precision's table (one and two nodes per thread) merged:
+// every slot takes the entry that is set.
+static Launchers merge_launchers(const Launchers& a, const Launchers& b) {
+  Launchers m = a;
+  for (int s = 0; s < NSHAPES; ++s) {
+    if (!m.bulk[s]) m.bulk[s] = b.bulk[s];
+    if (!m.bulk_tma[s]) m.bulk_tma[s] = b.bulk_tma[s];
+    if (!m.bulk_tma1[s]) m.bulk_tma1[s] = b.bulk_tma1[s];
+  }
+  return m;
+}
+struct MergedLauncherTables {
+  Launchers t[4][MAXS + 1];
+  MergedLauncherTables() {
+    const Launchers* (*one[4])(int) = {launchers_f64, launchers_f32, launchers_f32h, launchers_f32b};
+    const Launchers* (*two[4])(int) = {launchers_f64_n2, launchers_f32_n2, launchers_f32h_n2, launchers_f32b_n2};
+    for (int p = 0; p < 4; ++p)
+      for (int ns = 0; ns <= MAXS; ++ns) t[p][ns] = merge_launchers(*one[p](ns), *two[p](ns));
+  }
+};
 
 const Launchers* launchers(int prec, int ns) {
+  static const MergedLauncherTables tables;
+  if (ns < 0 || ns > MAXS) return nullptr;
   switch (prec) {
-    case PSLBM_FP64: return launchers_f64(ns);
-    case PSLBM_FP32: return launchers_f32(ns);
-    case PSLBM_FP32_SOLUTE_F16: return launchers_f32h(ns);
-    case PSLBM_FP32_SOLUTE_BF16: return launchers_f32b(ns);
+    case PSLBM_FP64: return &tables.t[0][ns];
+    case PSLBM_FP32: return &tables.t[1][ns];
+    case PSLBM_FP32_SOLUTE_F16: return &tables.t[2][ns];
+    case PSLBM_FP32_SOLUTE_BF16: return &tables.t[3][ns];
   }
   return nullptr;
 }

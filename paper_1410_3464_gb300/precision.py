@@ -69,8 +69,9 @@ def scene(args):
         sc = inputs.bubble_grain(nx=args.nx, ny=args.ny, grain=(args.nx // 2, args.ny // 2, args.ny * 3 // 16),
                                  bubble=(args.nx * 3 // 16, args.ny // 2, args.ny * 5 // 32))
     else:
+        kw = {} if args.k1 is None else {"k1": args.k1}
         sc = inputs.porous_discs(nx=args.nx, ny=args.ny, seed=args.seed, bubbles=args.bubbles,
-                                 gas_yield=not args.no_gas_yield)
+                                 gas_yield=not args.no_gas_yield, **kw)
     p = dict(sc["params"])
     if args.rho_ref is not None:
         p["rho_ref"] = tuple(float(v) for v in args.rho_ref.split(","))
@@ -154,6 +155,7 @@ def main(argv=None):
     ap.add_argument("--save-fields", default=None, help="path prefix: save all fields at each checkpoint")
     ap.add_argument("--save-at", default="", help="checkpoints to save fields at (default: all)")
     ap.add_argument("--bubbles", type=int, default=None, help="gas bubbles seeded in the porous scene")
+    ap.add_argument("--k1", type=float, default=None, help="rate of R1 in the porous scene (default 1e-5)")
     ap.add_argument("--no-gas-yield", action="store_true",
                     help="porous scene without R1's gas product (stable on long lattices)")
     ap.add_argument("--rho-ref", default=None, help="population shift per fluid component, e.g. 0,0")

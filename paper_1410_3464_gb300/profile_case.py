@@ -4,8 +4,9 @@ what ncu measured on it.
     python -m paper_1410_3464_gb300.profile_case run [--warm 2] [--steps 3] [--only SHAPE:STAGING]
         porous discs 1024x512 (seed 1), FP32, three transported species: the
         bulk-kernel variants (tile 16x16 and 32x8, each with plain loads, TMA
-        2-stage and TMA D2Q9-box staging) in that order, each for --warm then
-        --steps single steps.  The working set (about 150 MB) is larger than
+        2-stage and TMA D2Q9-box staging; tiles 16x32 and 32x16, two nodes per
+        thread, with plain loads and D2Q9-box staging) in that order, each for
+        --warm then --steps single steps.  The working set (about 150 MB) is larger than
         the 129 MB L2, so DRAM counters mean something, and small enough for a
         multi-pass ncu capture.
     python -m paper_1410_3464_gb300.profile_case run --batch 32 [--warm 2] [--steps 3] [--only SHAPE:STAGING]
@@ -33,7 +34,7 @@ import statistics
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SHAPES = ((16, 16), (32, 8))
+SHAPES = ((16, 16), (32, 8), (16, 32), (32, 16))     # the last two: two nodes per thread, no staging 1
 STAGINGS = (0, 1, 2)
 STAGING_NAMES = {0: "plain loads", 1: "tma 2-stage", 2: "tma d2q9-box"}
 WORKLOAD = "porous discs 1024x512 (seed 1), FP32, 3 species"
@@ -55,7 +56,7 @@ def variant_name(shape, staging):
 
 
 def variants(only=None):
-    out = [(s, g) for s in SHAPES for g in STAGINGS]
+    out = [(s, g) for s in SHAPES for g in STAGINGS if g != 1 or s[0] * s[1] == 256]
     if only:
         sh, g = only.split(":")
         tx, ty = (int(v) for v in sh.split("x"))
@@ -112,6 +113,7 @@ def run(args):
             raise SystemExit("TMA staging unavailable on this device")
         vs = [v for v in variants(args.only) if not (args.fp64 and v[1] != 0)]
         for shape, g in vs:
+            sim.set_staging(-1)
             sim.set_tile_shape(*shape)
             sim.set_staging(g)
             for _ in range(args.warm + args.steps):

@@ -357,12 +357,14 @@ def test_step_counts_and_graph_replay(pslbm):
 
 
 def test_tile_shapes_and_autotune_agree(pslbm):
-    """The step kernels exist for 16x16 and 32x8 tiles; a run pinned to either
-    shape and an autotuned run (which times both on its first 8 steps) give
-    bit-identical fields, and the autotuned handle reports its choice."""
+    """The step kernels exist for 16x16 and 32x8 tiles (one node per thread)
+    and 16x32 and 32x16 tiles (two nodes per thread); a run pinned to any
+    shape and an autotuned run (which times the four on its first 16 steps:
+    rows of 600 bytes leave no staged variant) give bit-identical fields, and
+    the autotuned handle reports its choice."""
     sc = inputs.porous_discs(nx=150, ny=90, seed=21, slug=(12, 6))
     res = []
-    for shape in ((16, 16), (32, 8), (0, 0)):
+    for shape in ((16, 16), (32, 8), (16, 32), (32, 16), (0, 0)):
         with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"]) as s:
             s.set_tile_shape(*shape)
             s.step(40)
@@ -371,7 +373,7 @@ def test_tile_shapes_and_autotune_agree(pslbm):
             if shape != (0, 0):
                 assert (tx, ty) == shape
             else:
-                assert (tx, ty) in ((16, 16), (32, 8))
+                assert (tx, ty) in ((16, 16), (32, 8), (16, 32), (32, 16))
             res.append(s.read())
     for r in res[1:]:
         for k in ("rho1", "rho2", "ux", "uy", "conc", "type", "vol"):

@@ -163,7 +163,7 @@ def test_staging_availability(pslbm):
 
 
 def test_autotune_over_variants_agrees(pslbm):
-    """An autotuned run (four variants timed on its first 16 steps) equals a
+    """An autotuned run (ten variants timed on its first 40 steps) equals a
     run pinned to the plain 16x16 kernel."""
     sc = inputs.porous_discs(nx=128, ny=96, seed=7)
     ref = run(pslbm, sc, 50, pslbm.FP32, 0)
