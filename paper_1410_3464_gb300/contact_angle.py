@@ -1,6 +1,8 @@
 """Static contact angle of a droplet on a flat wall (App. A2), on the GPU path.
 
     python -m paper_1410_3464_gb300.contact_angle --w -0.4 -0.2 0 0.1 0.14 --steps 30000
+    python -m paper_1410_3464_gb300.contact_angle --w 0 --w2 -0.5 -1 -2 --steps 30000
+        (the interaction on the gas component instead: w_1w = w, w_2w = each --w2)
 
 Each run steps inputs.droplet(w=...) (201x201, rescaled C-S EOS at 0.65 T_c,
 walls at the top and bottom rows, periodic sides) on the FP64 path and
@@ -78,8 +80,8 @@ def contact_angle(rho1, wall_y=0.5, skip=4):
                 rho_l=rl, rho_g=rg, level=level)
 
 
-def run(w, steps=30000, radius=50.0, nx=201, ny=201, precision=None):
-    sc = inputs.droplet(nx=nx, ny=ny, radius=radius, w=w)
+def run(w, steps=30000, radius=50.0, nx=201, ny=201, precision=None, w2=0.0):
+    sc = inputs.droplet(nx=nx, ny=ny, radius=radius, w=w, w2=w2)
     prec = pslbm.FP64 if precision is None else precision
     t0 = time.time()
     with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], None, None, precision=prec) as s:
@@ -87,7 +89,7 @@ def run(w, steps=30000, radius=50.0, nx=201, ny=201, precision=None):
         s.sync()
         rho1 = s.read(pslbm.F_RHO1)["rho1"]
     out = contact_angle(rho1)
-    out.update(w=w, steps=steps, seconds=time.time() - t0, initial_radius=radius)
+    out.update(w=w, w2=w2, steps=steps, seconds=time.time() - t0, initial_radius=radius)
     return out
 
 
@@ -96,13 +98,16 @@ def main(argv=None):
     ap.add_argument("--w", type=float, nargs="+", default=[-0.4, -0.2, 0.0, 0.1, 0.14])
     ap.add_argument("--steps", type=int, default=30000)
     ap.add_argument("--radius", type=float, default=50.0)
+    ap.add_argument("--w2", type=float, nargs="+", default=[0.0],
+                    help="interaction on the gas component (every pair of --w and --w2 is run)")
     args = ap.parse_args(argv)
     rows = []
     for w in args.w:
-        try:
-            rows.append(run(w, args.steps, args.radius))
-        except pslbm.PslbmError as e:       # a run that left the EOS domain or diverged
-            rows.append(dict(w=w, steps=args.steps, failed=str(e)))
+        for w2 in args.w2:
+            try:
+                rows.append(run(w, args.steps, args.radius, w2=w2))
+            except pslbm.PslbmError as e:       # a run that left the EOS domain or diverged
+                rows.append(dict(w=w, w2=w2, steps=args.steps, failed=str(e)))
     print(json.dumps(dict(workload="droplet on a flat wall, 201x201, rescaled C-S EOS at 0.65 Tc, FP64",
                           runs=rows)), flush=True)
 

@@ -285,14 +285,14 @@ def beaker(nx=100, ny=160, grain=(50, 50, 15), level=100, k1=1e-5, r1_surface=10
     return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=conc, vol=None, params=p)
 
 
-def droplet(nx=201, ny=201, radius=50.0, w=0.0, width=2.0):
+def droplet(nx=201, ny=201, radius=50.0, w=0.0, width=2.0, w2=0.0):
     """Static contact angle (App. A2): a semicircular liquid droplet of the
     given radius centred on the bottom wall of an nx x ny domain with walls at
     the top and bottom rows and periodic sides; rescaled C-S EOS at 0.65 T_c
     (liquid 8.17 / gas 0.0537, density ratio about 150); tau = 1; no species.
     The wall faces sit halfway between the wall rows and the first fluid rows
-    (y = 0.5 and y = ny - 1.5).  The solid-fluid interaction w of Eq. 16 acts
-    on the liquid component (w_1w = w); the gas component has none (w_2w = 0)."""
+    (y = 0.5 and y = ny - 1.5).  The solid-fluid interaction of Eq. 16 is
+    w_1w = w on the liquid component and w_2w = w2 on the gas component."""
     y, x = np.mgrid[0:ny, 0:nx]
     xc, yw = (nx - 1) / 2.0, 0.5
     r = np.hypot(x - xc, y - yw)
@@ -308,7 +308,7 @@ def droplet(nx=201, ny=201, radius=50.0, w=0.0, width=2.0):
     rho2 = np.where(fluid, rho2, 0.0)
     p = base_params(nx, ny)
     p.update(periodic_x=1, periodic_y=0, eos_a=CS_RESCALED["eos_a"], eos_b=CS_RESCALED["eos_b"],
-             eos_R=CS_RESCALED["eos_R"], eos_T=0.65 * CS_RESCALED["Tc"], w_adh=(float(w), 0.0),
+             eos_R=CS_RESCALED["eos_R"], eos_T=0.65 * CS_RESCALED["Tc"], w_adh=(float(w), float(w2)),
              rho_ref=(rl, 1e-4), rho_ref_gas=(rg, 0.05))
     return Scene(mask=mask, rho1=rho1, rho2=rho2, conc=None, vol=None, params=p)
 

@@ -2,9 +2,10 @@
 
     python -m paper_1410_3464_gb300.throughput --workload large --steps 300
         porous discs 4096x2048 (seed 4), one simulation.  At this size the
-        seeded scenes leave the EOS domain after a few hundred to a few
-        thousand steps (seed 4 lasts longest, past 2,250 steps), so the run is
-        a throughput measurement of 340 steps, not a long simulation
+        seeded scenes with all reactions leave the EOS domain after a few
+        hundred to a few thousand steps (seed 4 lasts longest, past 2,250
+        steps), so the run is a throughput measurement of 345 steps, not a
+        long simulation
     python -m paper_1410_3464_gb300.throughput --workload plain --steps 2000
         the plain-method scene (128x64, one grain, one bubble, 2 species), FP64
     python -m paper_1410_3464_gb300.throughput --workload porous-fp64 --steps 300
@@ -14,6 +15,11 @@
         (multiples of 16), porosity U[0.4, 0.8], rates log-uniform 1e-6-1e-1,
         stepped together as one batch (one launch per kernel per step over the
         packed tile list, CUDA graphs of up to 32 steps)
+    python -m paper_1410_3464_gb300.throughput --workload batch --variants [--trials 5]
+        every bulk-kernel variant (tile shape, nodes per thread, staging)
+        fixed in turn on the workload (large, batch, or porous: 1024x512 seed
+        1 with L2 flushed before every step): median over --trials profiled
+        steps of the bulk kernel's and the whole step's CUDA-event time
 
 The large-lattice and batch working sets exceed the 129 MB L2 by an order of
 magnitude, so no flush is needed between steps; the plain scene (3.7 MB in
@@ -73,7 +79,7 @@ def large(args, precision=pslbm.FP32, scene=None, name=None):
     fs = 8 if precision == pslbm.FP64 else 4
     with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
                           precision=precision) as s:
-        s.step(40)                       # autotuning (24 steps) and warm-up
+        s.step(45)                       # autotuning (up to 10 variants x 4 steps) and warm-up
         s.sync()
         el = timed(s.step, args.steps, stream)
         s.sync()
@@ -103,7 +109,7 @@ def batch(args):
     sims = [pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
                              precision=pslbm.FP32) for sc in scenes]
     b = pslbm.Batch(sims)
-    b.step(40)                           # autotuning and warm-up
+    b.step(45)                           # autotuning (up to 10 variants x 4 steps) and warm-up
     b.sync()
     el = timed(b.step, args.steps, stream)
     b.sync()
@@ -131,9 +137,74 @@ def batch(args):
                 tile=f"{tx}x{ty}", staging=STAGING_NAMES[staged], scene_generation_s=gen_s)
 
 
+# Bulk-kernel variants: (tile shape, staging); the two-node shapes (16x32,
+# 32x16) have no staging 1.
+VARIANTS = [((16, 16), 0), ((16, 16), 1), ((16, 16), 2), ((32, 8), 0), ((32, 8), 1), ((32, 8), 2),
+            ((16, 32), 0), ((16, 32), 2), ((32, 16), 0), ((32, 16), 2)]
+
+
+def variants(args):
+    import statistics
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if args.workload == "porous" else None
+
+    def time_one(obj):
+        obj.step(2)
+        ts = []
+        for _ in range(args.trials + 1):
+            if flush is not None:
+                flush.zero_()
+            ts.append(obj.profile_step(1))
+        ts = ts[1:]
+        return dict(bulk_ms=statistics.median(t[0]["bulk"] for t in ts),
+                    step_ms=statistics.median(t[1] for t in ts))
+
+    def name(shape, sg):
+        npt = shape[0] * shape[1] // 256
+        return f"{shape[0]}x{shape[1]} ({npt} node{'s' if npt > 1 else ''}/thread), {STAGING_NAMES[sg]}"
+
+    res = {}
+    if args.workload == "batch":
+        reqs = inputs.request_stream(args.instances, seed=args.seed, size_range=(128, 1024),
+                                     budget_range=(1000, 10000), rate_range=(1e-6, 1e-1),
+                                     porosity_range=(0.4, 0.8), stop_fraction=0.0)
+        sims = [pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                                 precision=pslbm.FP32) for sc in (inputs.request_scene(r) for r in reqs)]
+        for shape, sg in VARIANTS:
+            b = pslbm.Batch(sims, *shape)
+            if sg and not b.staging()[1]:
+                b.close()
+                continue
+            b.set_staging(sg)
+            res[name(shape, sg)] = time_one(b)
+            b.close()
+        for s in sims:
+            s.close()
+        what = f"{args.instances} porous geometries (seed {args.seed}), FP32, one batch"
+    else:
+        if args.workload == "porous":
+            args.nx, args.ny, args.seed = 1024, 512, 1
+        sc = inputs.porous_discs(nx=args.nx, ny=args.ny, seed=args.seed)
+        with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
+                              precision=pslbm.FP32) as s:
+            for shape, sg in VARIANTS:
+                if sg and not s.staging()[1]:
+                    continue
+                s.set_staging(-1)
+                s.set_tile_shape(*shape)
+                s.set_staging(sg)
+                res[name(shape, sg)] = time_one(s)
+        what = f"porous discs {args.nx}x{args.ny} (seed {args.seed}), FP32, one simulation" + (
+            ", L2 flushed before every step" if flush is not None else "")
+    best = min(res, key=lambda k: res[k]["bulk_ms"])
+    return dict(workload=what, trials=args.trials, unit="ms (CUDA events, median)", variants=res, fastest=best)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", choices=["large", "batch", "plain", "porous-fp64"], default="large")
+    ap.add_argument("--workload", choices=["large", "batch", "plain", "porous-fp64", "porous"], default="large")
+    ap.add_argument("--variants", action="store_true", help="time every bulk-kernel variant (large, batch, porous)")
+    ap.add_argument("--trials", type=int, default=5)
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--instances", type=int, default=256)
@@ -142,6 +213,13 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.seed is None:
         args.seed = 4
+    if args.variants:
+        if args.workload not in ("large", "batch", "porous"):
+            raise SystemExit("--variants: workload large, batch or porous")
+        print(json.dumps(variants(args)), flush=True)
+        return
+    if args.workload == "porous":
+        raise SystemExit("--workload porous is for --variants (the bench times this lattice)")
     if args.workload == "large":
         out = large(args)
     elif args.workload == "batch":

@@ -185,6 +185,28 @@ def test_adhesion_force_sign_and_magnitude():
     assert np.all(np.abs(F1x) < 1e-15)
 
 
+def test_gas_component_adhesion_sign_and_magnitude():
+    """Eq. 16 for the gas component (psi_2 := rho_2): next to a flat wall below,
+    F_2w = -w_2w rho_2 (0, -(1/9 + 2/36)), so w_2w < 0 pulls the gas toward the
+    wall (the non-wetting calibration) with magnitude |w_2w| rho_2 / 6; the
+    liquid component feels nothing from it, rows between the walls feel no
+    wall, and the top row (a wall beyond the non-periodic edge) is pulled up."""
+    nx, ny = 8, 6
+    p = lbm.default_params(nx, ny)
+    p.update(periodic_x=1, periodic_y=0, G12=0.0, G21=0.0, w_adh=(0.0, -4.0))
+    m = uniform_mask(nx, ny)
+    m[0, :] = lbm.WALL
+    rho2 = np.full((ny, nx), 0.05)
+    L = _lattice_with_density(np.full((ny, nx), 0.3), rho2, p, m)
+    r1, r2, _, _ = L.moments()
+    F1x, F1y, F2x, F2y = L._forces(L.type, r1, r2, 0 * r1, 0 * r1)
+    assert abs(F2y[1, 0] - (-4.0 * 0.05 / 6.0)) < 1e-15
+    assert np.all(np.abs(F2y[2:ny - 1]) < 1e-15)
+    assert abs(F2y[ny - 1, 0] - 4.0 * 0.05 / 6.0) < 1e-15
+    assert np.all(np.abs(F2x) < 1e-15)
+    assert np.all(np.abs(F1y) < 1e-15) and np.all(np.abs(F1x) < 1e-15)
+
+
 def test_flat_wall_is_a_mirror_for_the_cohesion_sums():
     """Walls are 90-degree walls (App. A2, Section 5): in the Eq. 11 and 14 sums
     a solid neighbour takes its mirror image across a flat wall, so next to a
