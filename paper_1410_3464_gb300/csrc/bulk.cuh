@@ -678,6 +678,24 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
         }
       }
 
+      // ---- push targets, shared by both components: the slot that the
+      // population moving along a lands in (slot a of the fluid neighbour, or
+      // slot OPP(a) here when it bounces back from a solid or wall), whether it
+      // is stored (nothing goes into a reservoir), and whether the node that
+      // receives it is marked liquid (the shift it is stored relative to)
+      int pdst[9];
+      unsigned pkeep = 0u, pliq = 0u;
+#pragma unroll
+      for (int a = 1; a < 9; ++a) {
+        const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
+        const bool fl = (c & C_FLUID) != 0;
+        pdst[a] = fl ? a * N + nb[a] : OPP(a) * N + node;
+        pkeep |= (fl || !(c & C_RES)) ? (1u << a) : 0u;
+        pliq |= (fl ? (c & C_MARK) != 0 : liq) ? (1u << a) : 0u;
+        // a liquid node flags the minerals on its axis links for the VOP kernel
+        if (a < 5 && liq && (c & C_MIN)) atomicOr(&V.vmask[nb[a] >> 5], 1u << (nb[a] & 31));
+      }
+
       // ---- fluid collision (Eq. 6, Eq. 8 at u_eq) and push streaming.  The
       // collision runs relative to this node's shift; a value pushed into a node
       // whose new phase has another shift is re-based by w (shift - shift').
@@ -713,14 +731,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
           }
           // into a fluid neighbour (re-based to its new phase), or bounced back
           // here from a solid or wall; nothing into a reservoir
-          const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
-          const bool fl = (c & C_FLUID) != 0;
-          const R sto = fl ? ((c & C_MARK) ? dl : dg) : down;
-          const int off = fl ? a * N + nb[a] : OPP(a) * N + node;
-          if (fl || !(c & C_RES)) st<TF, R>(fo + off, rfma<R>(w, sto, fs));
-          // a liquid node flags the minerals on its axis links for the VOP kernel
-          if (s == 0 && a < 5 && liq && (c & C_MIN))
-            atomicOr(&V.vmask[nb[a] >> 5], 1u << (nb[a] & 31));
+          const R sto = ((pliq >> a) & 1u) ? dl : dg;
+          if ((pkeep >> a) & 1u) st<TF, R>(fo + pdst[a], rfma<R>(w, sto, fs));
         }
       }
 
@@ -738,21 +750,21 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
             // the rest population stays; a moving one goes into a liquid
             // neighbour, out into a liquid reservoir, or bounces back here
             // (no-flux / mineral link)
-            int dst = node, slot = a;
+            // so: slot * N + destination node, the same for every species
+            int so = a * N + node;
             bool keep = true;
             if (a > 0) {
               const int c = int((nbits >> (4 * (a - 1))) & 0xFu);
               const bool into = (c & (C_FLUID | C_MARK)) == (C_FLUID | C_MARK);
               const bool out = (c & (C_RES | C_MARK)) == (C_RES | C_MARK);
-              dst = into ? nb[a] : node;
-              slot = (into || out) ? a : OPP(a);
+              so = ((into || out) ? a : OPP(a)) * N + (into ? nb[a] : node);
               keep = !out;
             }
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
               const R ja = a == 0 ? rp<R>(P).J0[k] : rp<R>(P).Ja[k];
               const R gs_ = bgk<R>(gs[k][a], geq[k][a], rp<R>(P).inv_tau_g[k], ja, Sk[k]);
-              if (keep) gst<TG, R>(P, k, gout + (k * 5 + slot) * N + dst, gs_);
+              if (keep) gst<TG, R>(P, k, gout + k * 5 * N + so, gs_);
             }
           }
         } else {
