@@ -44,8 +44,8 @@ def kernel_source_hash(precision="fp32"):
     """Hash of the device sources the bulk kernels of a precision are compiled from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1410_3464_gb300", "csrc")
-    unit = {"fp32": "kernels_f32.cu", "fp64": "kernels_f64.cu"}[precision]
-    for f in ("device.cuh", "tma.cuh", "bulk.cuh", "kernels_impl.cuh", unit):
+    units = {"fp32": ("kernels_f32.cu", "kernels_f32_n2.cu"), "fp64": ("kernels_f64.cu", "kernels_f64_n2.cu")}[precision]
+    for f in ("device.cuh", "tma.cuh", "bulk.cuh", "kernels_impl.cuh") + units:
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
