@@ -793,7 +793,8 @@ __device__ __forceinline__ bool bulk_tile(const Tile& tl, const StepView<TF, TG,
 
 // Plain bulk kernel: persistent over the tile list, populations loaded from
 // global memory by each thread.  The shared stage is double-buffered, so a
-// tile costs one block barrier.
+// tile costs one block barrier.  Blocks claim their tiles in list order from
+// a counter, so that blocks that meet cheap tiles take more of them.
 //
 // SINGLE: every tile belongs to the one simulation at insts[0]; its step view
 // is read once, the next tile's descriptor is loaded a tile ahead, and the
@@ -805,10 +806,17 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R, SH::NPT>()) k_bul
                                                                          const DevInst* __restrict__ insts) {
   __shared__ Pot<R> s_pot[2][SH::EXT];
   __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
+  __shared__ int s_claim[2];
   const int stride = gridDim.x;
   TileAcc<R> acc{R(-1.0 / 0.0), 0u};
   int buf = 0;
   TileTypes<SH::NPT> tt;
+  // after its first tile (blockIdx.x) a block claims its tiles in list order
+  // from the launch's counter (in the first instance), one tile ahead: lane 0
+  // of the last warp (no ring node) claims tile j+2 during tile j and shares it
+  // through shared memory, read after the tile's barrier
+  constexpr int CLAIMER = NTHREADS - 32;
+  auto claim = [&] { return stride + (int)atomicAdd(insts->scal + S_TILES, 1ULL); };
   if constexpr (SINGLE) {
     // one simulation: all tiles are live or none is
     if (!(insts->scal[S_STEP] < insts->scal[S_LIMIT])) return;
@@ -817,34 +825,43 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R, SH::NPT>()) k_bul
     const GlobalSrc<TF, TG, R, NS> src{V.fin, V.gin, V.N};
     int ti = blockIdx.x;
     Tile tl = ti < ntiles ? tiles[ti] : Tile{};
+    if (threadIdx.x == CLAIMER) s_claim[0] = claim();
     if (ti < ntiles) tt = load_types<SH>(tl, P, V.tin, threadIdx.x);
+    __syncthreads();
+    int j = 0;
     while (ti < ntiles) {
-      const int nt = ti + stride;
+      const int nt = s_claim[j & 1];
       const Tile tn = nt < ntiles ? tiles[nt] : Tile{};
+      if (threadIdx.x == CLAIMER) s_claim[(j & 1) ^ 1] = claim();
       auto next_types = [&](TileTypes<SH::NPT>& t) {
         if (nt < ntiles) t = load_types<SH>(tn, P, V.tin, threadIdx.x);
       };
       bulk_tile<SH, TF, TG, R, NS>(tl, V, P, src, [] {}, next_types, true, tt, acc, s_pot[buf], s_t[buf],
                                    s_m[buf]);
       buf ^= 1;
+      ++j;
       ti = nt;
       tl = tn;
     }
     flush_acc(acc, V.scal, V.cur);
   } else {
     // a batch: consecutive tiles of a block often belong to one instance (a
-    // large member spans many grid strides), so the instance's view and step
-    // limit are read, and its maximum and status flushed, only when the
-    // instance changes; tile descriptors ride a tile ahead
+    // large member spans many tiles), so the instance's view and step limit
+    // are read, and its maximum and status flushed, only when the instance
+    // changes; tile descriptors ride a tile ahead
     int ti = blockIdx.x;
     Tile tl = ti < ntiles ? tiles[ti] : Tile{};
     int vinst = -1;            // instance of the run in progress
     bool vlive = false;        // ... below its step limit
     bool have_tt = false;      // tt holds the current tile's types
     StepView<TF, TG, R> V{};
+    if (threadIdx.x == CLAIMER) s_claim[0] = claim();
+    __syncthreads();
+    int j = 0;
     while (ti < ntiles) {
-      const int nt = ti + stride;
+      const int nt = s_claim[j & 1];
       const Tile tn = nt < ntiles ? tiles[nt] : Tile{};
+      if (threadIdx.x == CLAIMER) s_claim[(j & 1) ^ 1] = claim();
       if (tl.inst != vinst) {
         if (vlive) flush_acc(acc, V.scal, V.cur);
         vinst = tl.inst;
@@ -865,7 +882,12 @@ __global__ void __launch_bounds__(NTHREADS, bulk_min_blocks<R, SH::NPT>()) k_bul
                                      s_m[buf]);
         buf ^= 1;
         have_tt = same;
+      } else {
+        // a frozen member: nothing to compute, but the claim made during this
+        // tile is read after a barrier
+        __syncthreads();
       }
+      ++j;
       ti = nt;
       tl = tn;
     }
@@ -1001,8 +1023,13 @@ __device__ __forceinline__ void stage_issue(const Tile& d, const CUtensorMap* mf
 //     (fewer registers, 70 KB of shared memory).  The stage of tile j is read
 //     until the end of tile j, so the copy of tile j+1 goes into tile j-1's
 //     stage right after tile j's barrier.
-// Blocks walk the tile list with the grid stride; tile descriptors ride two
-// tiles ahead in registers.  SINGLE: every tile belongs to the one simulation
+// Each block takes tiles blockIdx.x and blockIdx.x + gridDim.x, then claims
+// further tiles in list order from a counter (lane 0 of the last warp, which
+// has no ring node and so time to spare before the barrier, claims tile j+2
+// while the block computes tile j-1 and shares it through shared memory), so
+// that blocks that meet cheap tiles take more of them and the launch does not
+// end with a few blocks still working; tile descriptors ride two tiles ahead
+// in registers.  SINGLE: every tile belongs to the one simulation
 // at insts[0], whose parameter block comes as a kernel argument (read from the
 // constant bank, uniform across the grid); its step view and population maps
 // are read once and the maximum and status flushed once at the end.
@@ -1036,8 +1063,10 @@ __global__ void __launch_bounds__(NTHREADS, tma_min_blocks<SH, MODE>())
   __shared__ Pot<R> s_pot[2][SH::EXT];
   __shared__ uint8_t s_t[2][SH::EXT], s_m[2][SH::EXT];
   __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_claim[2];
 
   const int stride = gridDim.x;
+  constexpr int CLAIMER = NTHREADS - 32;   // the thread that claims tiles
   View V{};
   if constexpr (SINGLE) {
     // one simulation: all tiles are live or none is
@@ -1061,11 +1090,18 @@ __global__ void __launch_bounds__(NTHREADS, tma_min_blocks<SH, MODE>())
     }
     stage_issue<SH, TG, NS, SG>(d, &Ip->tmf[SHAPE][cur], &Ip->tmg[SHAPE][cur], stage, bar);
   };
+  // the next tile of this block from the launch's claim counter (in the first
+  // instance; V.scal is that instance's for one simulation)
+  auto claim = [&] {
+    unsigned long long* c = (SINGLE ? V.scal : insts->scal) + S_TILES;
+    return 2 * stride + (int)atomicAdd(c, 1ULL);
+  };
   // tile descriptors ride two tiles ahead in registers
   int ti = blockIdx.x;
   int t1 = ti + stride;
   Tile d0 = ti < ntiles ? tiles[ti] : Tile{};
   Tile d1 = t1 < ntiles ? tiles[t1] : Tile{};
+  if (threadIdx.x == CLAIMER) s_claim[0] = claim();
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -1089,8 +1125,11 @@ __global__ void __launch_bounds__(NTHREADS, tma_min_blocks<SH, MODE>())
   uint32_t phase = 0;               // parity bit per stage
   while (ti < ntiles) {
     const int b = j & 1;                          // stage and shared buffers of this tile
-    const int t2 = t1 + stride;
+    // tile j+2 was claimed during tile j-1 (or before the first tile); claim
+    // tile j+3 now (read at the top of tile j+1, after this tile's barrier)
+    const int t2 = s_claim[b];
     const Tile d2 = t2 < ntiles ? tiles[t2] : Tile{};
+    if (threadIdx.x == CLAIMER) s_claim[b ^ 1] = claim();
     const bool ok = mbar_wait_bounded(&bars[b], (phase >> b) & 1u);
     phase ^= 1u << b;
     if constexpr (!SINGLE) {

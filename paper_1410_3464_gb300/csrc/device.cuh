@@ -60,7 +60,9 @@ enum {
   S_LIMIT = 5,     // step limit: an instance at or past it is frozen (kernels skip it)
   S_THETA = 6,     // this step's liquid threshold (half the previous maximum), FP64 bits
   S_THETAF = 7,    // the same rounded to FP32 (bits in the low word)
-  S_NSCAL = 8
+  S_TILES = 8,     // tiles claimed so far by the bulk launch in progress (first instance of a
+                   // launch only; the amendment kernel sets it back to zero after every launch)
+  S_NSCAL = 9
 };
 enum { ST_NONFINITE = 1, ST_EOS = 2, ST_EVOVERFLOW = 4, ST_TIMEOUT = 8 };
 

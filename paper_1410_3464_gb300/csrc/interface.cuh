@@ -213,6 +213,8 @@ __device__ __forceinline__ void finish_step(const DevInst* Ip, unsigned long lon
 
 template <class TF, class TG, class R, int NS>
 __global__ void __launch_bounds__(NTHREADS) k_amend(const DevInst* __restrict__ insts) {
+  // the bulk kernel's tile claims start from zero at its next launch
+  if (blockIdx.x == 0 && threadIdx.x == 0) insts[0].scal[S_TILES] = 0ULL;
   const DevInst* Ip = insts + blockIdx.x;
   // the counters this kernel reads, loaded together (one memory round trip)
   const volatile unsigned long long* sc = Ip->scal;
