@@ -315,7 +315,7 @@ def ours_arm(args):
     trials = None
     if batch:
         runner = pslbm.Batch(sims)
-        runner.step(45)              # variant autotuning (10 variants x 4 steps) and a first warm-up
+        runner.step(90)              # variant autotuning (10 variants x 4 steps, twice) and a first warm-up
     else:
         # one lattice: each variant timed for 5 steps under the timed loop's own
         # conditions (L2 flushed before every step for the 1024x512 lattice)
@@ -408,7 +408,7 @@ def ours_arm(args):
                   "not flushed: the state is far larger than the 129 MB L2"),
            "parallelism": f"{'instances sharded over' if batch else 'replicas on'} {ws} GPU(s), no data-path exchange",
            "tile": f"{tshape[0]}x{tshape[1]}", "staging": STAGING_NAMES[staged],
-           "variant_choice": ("the library's autotuner (each open variant timed for 3 steps)" if trials is None else
+           "variant_choice": ("the library's autotuner (each open variant timed for 3 steps, in two passes, best pass kept)" if trials is None else
                               "each variant timed for 5 steps under the timed loop's conditions: " +
                               ", ".join(f"{k[0][0]}x{k[0][1]} {STAGING_NAMES[k[1]]} {v:.4f} ms"
                                         for k, v in sorted(trials.items())))}

@@ -200,8 +200,9 @@ pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes)
  * 256-thread block: 16x16 or 32x8 (one node per thread), 16x32 or 32x16 (two
  * nodes per thread: thread (tx, ty) computes rows ty and ty + 256 / tile_x).
  * (0, 0), the default, leaves the shape to timing: the next step call long
- * enough to try every open variant (tile shape x staging, 4 steps each, which
- * advance the simulation like any others) times them and keeps the fastest;
+ * enough to try every open variant (tile shape x staging, 4 steps each, in
+ * two passes, the second in reverse order; the steps advance the simulation
+ * like any others) times them and keeps the fastest by its better pass;
  * the results do not depend on the variant.  tuned reports whether the variant
  * has been chosen (by timing, or because only one was left open).
  * PSLBM_ERR_PARAM for another shape, or for a two-node shape while staging 1

@@ -4,7 +4,7 @@
         porous discs 4096x2048 (seed 4), one simulation.  At this size the
         seeded scenes with all reactions leave the EOS domain after a few
         hundred to a few thousand steps (seed 4 lasts longest, past 2,250
-        steps), so the run is a throughput measurement of 345 steps, not a
+        steps), so the run is a throughput measurement of 390 steps, not a
         long simulation
     python -m paper_1410_3464_gb300.throughput --workload plain --steps 2000
         the plain-method scene (128x64, one grain, one bubble, 2 species), FP64
@@ -79,7 +79,7 @@ def large(args, precision=pslbm.FP32, scene=None, name=None):
     fs = 8 if precision == pslbm.FP64 else 4
     with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
                           precision=precision) as s:
-        s.step(45)                       # autotuning (up to 10 variants x 4 steps) and warm-up
+        s.step(90)                       # autotuning (up to 10 variants x 4 steps, twice) and warm-up
         s.sync()
         el = timed(s.step, args.steps, stream)
         s.sync()
@@ -109,7 +109,7 @@ def batch(args):
     sims = [pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
                              precision=pslbm.FP32) for sc in scenes]
     b = pslbm.Batch(sims)
-    b.step(45)                           # autotuning (up to 10 variants x 4 steps) and warm-up
+    b.step(90)                           # autotuning (up to 10 variants x 4 steps, twice) and warm-up
     b.sync()
     el = timed(b.step, args.steps, stream)
     b.sync()

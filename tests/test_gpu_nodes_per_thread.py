@@ -203,10 +203,10 @@ def test_two_node_shapes_stage_the_d2q9_box_only(pslbm):
         assert s.tile_shape()[:2] == (32, 8)
         with pytest.raises(pslbm.PslbmError):
             s.set_tile_shape(64, 4)
-    ref = run(pslbm, sc, 60, pslbm.FP32, (32, 16))
+    ref = run(pslbm, sc, 100, pslbm.FP32, (32, 16))
     with pslbm.Simulation(sc["mask"], sc["params"], sc["rho1"], sc["rho2"], sc["conc"], sc["vol"],
                           precision=pslbm.FP32) as s:
-        s.step(60)
+        s.step(100)
         tx, ty, tuned = s.tile_shape()
         assert tuned and (tx, ty) in ((16, 16), (32, 8), (16, 32), (32, 16))
         staged, _ = s.staging()

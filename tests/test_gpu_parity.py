@@ -359,8 +359,8 @@ def test_step_counts_and_graph_replay(pslbm):
 def test_tile_shapes_and_autotune_agree(pslbm):
     """The step kernels exist for 16x16 and 32x8 tiles (one node per thread)
     and 16x32 and 32x16 tiles (two nodes per thread); a run pinned to any
-    shape and an autotuned run (which times the four on its first 16 steps:
-    rows of 600 bytes leave no staged variant) give bit-identical fields, and
+    shape and an autotuned run (which times the four twice on its first 32
+    steps: rows of 600 bytes leave no staged variant) give bit-identical fields, and
     the autotuned handle reports its choice."""
     sc = inputs.porous_discs(nx=150, ny=90, seed=21, slug=(12, 6))
     res = []

@@ -50,7 +50,7 @@ def test_batch_members_with_different_limits(pslbm):
     for s, n in zip(sims, limits):
         s.set_step_limit(n)
     b = pslbm.Batch(sims)
-    b.step(45)
+    b.step(90)
     b.sync()
     b.close()
     for s, n, ref in zip(sims, limits, refs):
