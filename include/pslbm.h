@@ -163,7 +163,12 @@ pslbm_status pslbm_set_stream(void* cuda_stream);
  *   p         parameters (validated: PSLBM_ERR_PARAM on invalid values, incl.
  *             tau <= 0.5, k >= (1 - J0)/2 for a reactive species, bad indices).
  * On success *out holds a new handle; on failure *out is NULL and nothing leaks.
- * The initial liquid threshold is half the maximum initial rho1 over fluid nodes. */
+ * The initial liquid threshold is half the maximum initial rho1 over fluid nodes.
+ * The handle's device state is one allocation (pslbm_device_bytes; the tile
+ * lists of the step kernels are allocated on demand); the inputs are copied
+ * with cudaMemcpyAsync on the library stream (page-locked host buffers copy
+ * fastest) and the call synchronises once before it returns, after which the
+ * caller may reuse them. */
 pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double* rho2,
                           const double* conc, const double* vol,
                           const pslbm_params* p, pslbm_t* out);

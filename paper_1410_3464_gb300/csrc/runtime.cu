@@ -453,6 +453,29 @@ pslbm_status profile_steps(Stepper& st, int64_t n, double* kernel_ms, double* to
   return PSLBM_OK;
 }
 
+// Initial solid volumes from the node types when the caller gives none:
+// V_D = 1 at D(s) nodes, V_F = 1 at F(s) nodes, 0 elsewhere.
+__global__ void k_vol_from_mask(const uint8_t* __restrict__ mask, double* __restrict__ V, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const int t = mask[i] & 15;
+    V[i] = t == PSLBM_SOLID_D ? 1.0 : 0.0;
+    V[N + i] = t == PSLBM_SOLID_F ? 1.0 : 0.0;
+  }
+}
+
+// First step's liquid threshold from the initial maximum of rho_1 over fluid
+// nodes (res[0], -inf without fluid): the maximum in the ordered encoding of
+// the step's slot, and half of it in both precisions, as the amendment kernel
+// leaves them at the end of a step.
+__global__ void k_first_threshold(const double* __restrict__ res, unsigned long long* __restrict__ scal) {
+  const double m = res[0];
+  const unsigned long long enc = m > -INFINITY ? ord_enc(m) : 0ULL;
+  const double th = 0.5 * ord_dec(enc);
+  scal[S_MAX0] = enc;
+  scal[S_THETA] = (unsigned long long)__double_as_longlong(th);
+  scal[S_THETAF] = (unsigned long long)(unsigned)__float_as_int(__double2float_rn(th));
+}
+
 // Step count and status bits of every member of a batch, gathered into one
 // device buffer (out[2 i], out[2 i + 1]) for a single copy to the host.
 __global__ void k_batch_monitor(const DevInst* __restrict__ insts, int n, unsigned long long* __restrict__ out) {
@@ -752,43 +775,50 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
   I.N = N;
   I.evcap = (int)N;
   pslbm_status st = PSLBM_OK;
-  void* ptr;
-#define AL(field, bytes)                                     \
-  do {                                                       \
-    st = dalloc(h, &ptr, (bytes));                           \
-    if (st != PSLBM_OK) goto fail_cleanup;                   \
-    field = decltype(field)(ptr);                            \
-  } while (0)
-  for (int b = 0; b < 2; ++b) {
-    AL(I.f[b], (size_t)N * 18 * fsize(p->precision));
-    AL(I.g[b], (size_t)N * 5 * ns * gsize(p->precision));
-    AL(I.type[b], (size_t)N);
-  }
-  AL(I.V, (size_t)N * 2 * sizeof(double));
-  AL(I.evt, (size_t)N);
-  AL(I.xs, (size_t)N * sizeof(double));
-  AL(I.evlist, (size_t)N * 2 * sizeof(int));
-  AL(I.claim, (size_t)N * sizeof(int));
-  AL(I.vmask, (size_t)((N + 31) / 32) * sizeof(unsigned));
-  AL(I.scal, S_NSCAL * sizeof(unsigned long long));
-  AL(h->d, sizeof(DevInst));
   {
-    // staging copies of the inputs
-    uint8_t* dmask = nullptr;
-    double *dr1 = nullptr, *dr2 = nullptr, *dc = nullptr;
-    void* tmp;
-    std::vector<void*> stage;
-    auto salloc = [&](void** pp, size_t b) {
-      cudaError_t e = cudaMalloc(pp, b ? b : 16);
-      if (e == cudaSuccess) stage.push_back(*pp);
-      return e;
-    };
-    cudaError_t e = salloc(&tmp, N);
-    dmask = (uint8_t*)tmp;
-    if (e == cudaSuccess) e = salloc(&tmp, N * sizeof(double)), dr1 = (double*)tmp;
-    if (e == cudaSuccess) e = salloc(&tmp, N * sizeof(double)), dr2 = (double*)tmp;
-    if (e == cudaSuccess && conc && ns) e = salloc(&tmp, N * ns * sizeof(double)), dc = (double*)tmp;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dmask, mask, N, cudaMemcpyHostToDevice, s);
+    // one device allocation holds the instance's whole state, each part on a
+    // 256-byte boundary (TMA wants 16-byte aligned bases); the initial
+    // threshold's budget partial sums are the last part
+    const size_t fb = (size_t)N * 18 * fsize(p->precision), gb = (size_t)N * 5 * ns * gsize(p->precision);
+    const size_t sizes[] = {fb, fb, gb, gb, (size_t)N, (size_t)N, (size_t)N * 2 * sizeof(double), (size_t)N,
+                            (size_t)N * sizeof(double), (size_t)N * 2 * sizeof(int), (size_t)N * sizeof(int),
+                            (size_t)((N + 31) / 32) * sizeof(unsigned), S_NSCAL * sizeof(unsigned long long),
+                            sizeof(DevInst), (size_t)(BUD_BLOCKS + 1) * NBUD * sizeof(double)};
+    constexpr int NPARTS = sizeof(sizes) / sizeof(sizes[0]);
+    size_t offs[NPARTS], total = 0;
+    for (int i = 0; i < NPARTS; ++i) {
+      offs[i] = total;
+      total += ((sizes[i] ? sizes[i] : 16) + 255) / 256 * 256;
+    }
+    void* arena = nullptr;
+    st = dalloc(h, &arena, total);
+    if (st != PSLBM_OK) goto fail_cleanup;
+    char* base = (char*)arena;
+    I.f[0] = base + offs[0];
+    I.f[1] = base + offs[1];
+    I.g[0] = base + offs[2];
+    I.g[1] = base + offs[3];
+    I.type[0] = (uint8_t*)(base + offs[4]);
+    I.type[1] = (uint8_t*)(base + offs[5]);
+    I.V = (double*)(base + offs[6]);
+    I.evt = (uint8_t*)(base + offs[7]);
+    I.xs = (double*)(base + offs[8]);
+    I.evlist = (int*)(base + offs[9]);
+    I.claim = (int*)(base + offs[10]);
+    I.vmask = (unsigned*)(base + offs[11]);
+    I.scal = (unsigned long long*)(base + offs[12]);
+    h->d = (DevInst*)(base + offs[13]);
+    double* part = (double*)(base + offs[14]);
+    double* res = part + (size_t)BUD_BLOCKS * NBUD;
+
+    // the inputs are staged in the second population buffer (at least 72
+    // bytes per node; they need 17 + 8 ns <= 49), which is cleared once the
+    // initialisation kernel has read them
+    double* dr1 = (double*)I.f[1];
+    double* dr2 = dr1 + N;
+    double* dc = (conc && ns) ? dr2 + N : nullptr;
+    uint8_t* dmask = (uint8_t*)(dr2 + N + (dc ? (size_t)N * ns : 0));
+    cudaError_t e = cudaMemcpyAsync(dmask, mask, N, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dr1, rho1, N * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dr2, rho2, N * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && dc) e = cudaMemcpyAsync(dc, conc, N * ns * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -797,19 +827,13 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
     if (e == cudaSuccess) e = cudaMemsetAsync(I.vmask, 0, (size_t)((N + 31) / 32) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.scal, 0, S_NSCAL * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(I.scal + S_LIMIT, 0xff, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(I.f[1], 0, (size_t)N * 18 * fsize(p->precision), s);
-    if (e == cudaSuccess && ns) e = cudaMemsetAsync(I.g[1], 0, (size_t)N * 5 * ns * gsize(p->precision), s);
+    if (e == cudaSuccess && ns) e = cudaMemsetAsync(I.g[1], 0, gb, s);
     if (e == cudaSuccess) {
       if (vol) {
         e = cudaMemcpyAsync(I.V, vol, (size_t)N * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
       } else {
-        std::vector<double> v0((size_t)N * 2, 0.0);
-        for (long long i = 0; i < N; ++i) {
-          v0[i] = (mask[i] & 15) == PSLBM_SOLID_D ? 1.0 : 0.0;
-          v0[N + i] = (mask[i] & 15) == PSLBM_SOLID_F ? 1.0 : 0.0;
-        }
-        e = cudaMemcpyAsync(I.V, v0.data(), (size_t)N * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        k_vol_from_mask<<<(unsigned)std::min<long long>((N + 255) / 256, 65536), 256, 0, s>>>(dmask, I.V, N);
+        e = cudaGetLastError();
       }
     }
     h->run.staged_ok = L->bulk_tma[0] != nullptr && encode_maps(I, p);
@@ -818,55 +842,24 @@ pslbm_status pslbm_create(const uint8_t* mask, const double* rho1, const double*
       L->init(s, h->d, dmask, dr1, dr2, dc, N);
       e = cudaGetLastError();
     }
+    // initial liquid threshold: half the maximum initial rho_1 over fluid
+    // nodes (the first budget entry), decoded on the device
+    if (e == cudaSuccess) {
+      L->budget(s, h->d, part, res);
+      k_first_threshold<<<1, 1, 0, s>>>(res, I.scal);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.f[1], 0, fb, s);
+    // the host copy of the descriptor is read by the copy above before the
+    // call returns only for pageable memory; synchronise once for it and for
+    // the errors of everything above
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (void* q : stage) cudaFree(q);
     if (e != cudaSuccess) {
       st = fail(nullptr, e == cudaErrorMemoryAllocation ? PSLBM_ERR_OOM : PSLBM_ERR_CUDA,
                 std::string("create: ") + cudaGetErrorString(e));
       goto fail_cleanup;
     }
   }
-  {
-    // initial liquid threshold: half the maximum initial rho_1 over fluid nodes
-    double* part = nullptr;
-    double* res = nullptr;
-    cudaError_t e = cudaMalloc(&part, BUD_BLOCKS * NBUD * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&res, NBUD * sizeof(double));
-    if (e == cudaSuccess) {
-      L->budget(s, h->d, part, res);
-      e = cudaGetLastError();
-    }
-    double b[NBUD];
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b, res, sizeof b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (part) cudaFree(part);
-    if (res) cudaFree(res);
-    if (e == cudaSuccess) {
-      unsigned long long enc = 0;
-      if (b[0] > -INFINITY) {
-        unsigned long long bits;
-        std::memcpy(&bits, &b[0], 8);
-        enc = (bits & 0x8000000000000000ULL) ? ~bits : (bits | 0x8000000000000000ULL);
-      }
-      // the first step's threshold, as the amendment kernel decodes it
-      const double th = 0.5 * ord_dec(enc);
-      const float thf = float(th);
-      unsigned long long slots[3] = {enc, 0, 0};
-      std::memcpy(&slots[1], &th, 8);
-      uint32_t fb;
-      std::memcpy(&fb, &thf, 4);
-      slots[2] = fb;
-      e = cudaMemcpyAsync(I.scal + S_MAX0, &slots[0], sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(I.scal + S_THETA, &slots[1], 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    }
-    if (e != cudaSuccess) {
-      st = fail(nullptr, PSLBM_ERR_CUDA, std::string("create threshold: ") + cudaGetErrorString(e));
-      goto fail_cleanup;
-    }
-  }
-#undef AL
   h->run.L = L;
   h->run.d = h->d;
   h->run.ninst = 1;
@@ -939,7 +932,8 @@ pslbm_status pslbm_estimate_device_bytes(const pslbm_params* p, uint64_t* bytes)
   uint64_t tiles = 0;
   for (int sh = 0; sh < NSHAPES; ++sh)
     tiles += ((uint64_t)(p->nx + SHAPE_TX[sh] - 1) / SHAPE_TX[sh]) * ((uint64_t)(p->ny + SHAPE_TY[sh] - 1) / SHAPE_TY[sh]);
-  *bytes = N * per + vmask_bytes + tiles * sizeof(Tile) + sizeof(DevInst) + S_NSCAL * 8 + 13 * 16;
+  *bytes = N * per + vmask_bytes + tiles * sizeof(Tile) + sizeof(DevInst) + S_NSCAL * 8 +
+           (uint64_t)(BUD_BLOCKS + 1) * NBUD * sizeof(double) + 15 * 256;
   return PSLBM_OK;
 }
 
