@@ -7,7 +7,8 @@
 //      of the resident simulations stays within the HBM budget (and below the
 //      resident cap);
 //   2. when the resident set changed, re-pack one batch per species count (one
-//      tile list and one launch per kernel for all its members);
+//      tile list and one launch per kernel for all its members), with the
+//      kernel variant the first batch of that species count chose by timing;
 //   3. advance every batch by `chunk_steps` steps; members whose step budget
 //      ends inside the chunk are frozen on the device at their budget;
 //   4. retire requests that reached their budget or whose total solid volume
@@ -58,6 +59,9 @@ struct pslbm_server_s {
   std::vector<Request*> active;
   std::map<uint64_t, std::unique_ptr<Request>> all;
   std::map<int, pslbm_batch_t> batches;   // by species count
+  // the kernel variant (tile x, tile y, staging) the first batch of a species
+  // count chose by timing, fixed for the batches re-packed after it
+  std::map<int, std::vector<int32_t>> variant;
   bool dirty = true;
   uint64_t used = 0;
   uint64_t next_id = 1;
@@ -222,16 +226,28 @@ pslbm_status pslbm_server_advance(pslbm_server_t s, int32_t* n_active, int32_t* 
     for (Request* r : s->active) groups[r->p.n_species].push_back(r->h);
     for (auto& kv : groups) {
       pslbm_batch_t b = nullptr;
-      pslbm_status st = pslbm_batch_create((int32_t)kv.second.size(), kv.second.data(), 0, 0, &b);
+      auto vk = s->variant.find(kv.first);
+      const bool known = vk != s->variant.end();
+      pslbm_status st = pslbm_batch_create((int32_t)kv.second.size(), kv.second.data(), known ? vk->second[0] : 0,
+                                           known ? vk->second[1] : 0, &b);
       if (st != PSLBM_OK) return sfail(s, st, pslbm_last_error(nullptr));
+      // a staging that the new mix does not allow falls back to plain loads
+      if (known && pslbm_batch_set_staging(b, vk->second[2]) != PSLBM_OK) pslbm_batch_set_staging(b, 0);
       s->batches[kv.first] = b;
     }
     s->dirty = false;
   }
-  // 3. one chunk of steps for every resident simulation
+  // 3. one chunk of steps for every resident simulation; the first batch of a
+  // species count that a chunk tuned leaves its variant for the later ones
   for (auto& kv : s->batches) {
     pslbm_status st = pslbm_batch_step(kv.second, s->cfg.chunk_steps);
     if (st != PSLBM_OK) return sfail(s, st, pslbm_last_error(nullptr));
+    if (!s->variant.count(kv.first)) {
+      int32_t tx = 0, ty = 0, tuned = 0, staged = 0, avail = 0;
+      if (pslbm_batch_get_tile_shape(kv.second, &tx, &ty, &tuned) == PSLBM_OK && tuned &&
+          pslbm_batch_get_staging(kv.second, &staged, &avail) == PSLBM_OK)
+        s->variant[kv.first] = {tx, ty, staged};
+    }
   }
   if (cudaStreamSynchronize((cudaStream_t)pslbm_get_stream()) != cudaSuccess)
     return sfail(s, PSLBM_ERR_CUDA, "stream synchronisation failed");
