@@ -600,6 +600,45 @@ def test_dissolution_flip_and_fill():
     assert L.V[0, 3, 3] == 0.0
 
 
+def test_dissolution_fill_closed_form():
+    """The S->L fill (Section 4.5, R9) and the reactive link rule (R7) by hand.
+    A uniform liquid at rest (no interactions, so it stays at rest and a
+    bounce-back returns what it receives) surrounds one D(s) node of tiny V_D.
+    In one step each of its four axis neighbours keeps all its populations but
+    the one that meets the mineral, which comes back as g_out (1 - kappa) /
+    (1 + kappa) (C_sat = 0, kappa = k2 / (2 J_a)); the node dissolves and is
+    refilled at rest with the neighbours' densities and the mean of their
+    concentrations: C0 (1 - J_a (1 - (1 - kappa) / (1 + kappa)) / J ), J = 1."""
+    nx, ny = 7, 7
+    p = flow_off(lbm.default_params(nx, ny))
+    J0, k2, C0, r1, r2 = 1 / 3, 0.05, 0.7, 1.0, 0.015
+    p.update(periodic_x=1, periodic_y=1, n_species=1, idx_B=0, J0=(J0, 0, 0, 0), tau_g=(0.8, 1, 1, 1),
+             k2=k2, Vbar_D=1.0)
+    m = uniform_mask(nx, ny)
+    m[3, 3] = lbm.SOLID_D
+    vol = np.zeros((2, ny, nx))
+    vol[0, 3, 3] = 1e-6
+    L = lbm.Lattice(m, p, np.full((ny, nx), r1), np.full((ny, nx), r2), np.full((1, ny, nx), C0), vol)
+    L.theta = 0.5
+    L.step()
+    Ja = (1 - J0) / 4
+    kappa = k2 / (2 * Ja)
+    c_nbr = C0 - Ja * C0 + Ja * C0 * (1 - kappa) / (1 + kappa)
+    fl = L.fields()
+    assert L.type[3, 3] == lbm.LIQUID
+    for q in [(3, 4), (4, 3), (3, 2), (2, 3)]:
+        assert abs(fl["conc"][0][q] - c_nbr) < 1e-15
+    for q in [(2, 2), (2, 4), (4, 2), (4, 4), (0, 0)]:
+        assert abs(fl["conc"][0][q] - C0) < 1e-15
+    assert abs(fl["conc"][0][3, 3] - c_nbr) < 1e-15
+    assert abs(fl["rho1"][3, 3] - r1) < 1e-15 and abs(fl["rho2"][3, 3] - r2) < 1e-15
+    assert abs(fl["ux"][3, 3]) < 1e-15 and abs(fl["uy"][3, 3]) < 1e-15
+    for a in range(9):
+        assert abs(L.f[0, a, 3, 3] - lbm.W9[a] * r1) < 1e-15
+        assert abs(L.f[1, a, 3, 3] - lbm.W9[a] * r2) < 1e-15
+    assert L.V[0, 3, 3] == 0.0
+
+
 def test_overflow_flip_conserves_volume_and_mass():
     """Precipitation overflow (VOP): a node whose volume reaches V_split keeps
     1 and puts the excess into the liquid neighbour picked by SplitMix64; the
