@@ -236,7 +236,7 @@ pslbm_status pslbm_get_staging(pslbm_t h, int32_t* staged, int32_t* available);
  * density over fluid nodes found by the last step (the quantity whose half is
  * the next liquid threshold, Section 4.5; the initial maximum before the first
  * step) and the device status bits (1 non-finite density, 2 EOS domain,
- * 4 event-list overflow, 8 staged-copy timeout).  Reads 64 bytes from the
+ * 4 event-list overflow, 8 staged-copy timeout).  Reads 72 bytes from the
  * device and synchronises the library stream; no kernel runs.  Returns the
  * matching error status when a bit is set (sticky, as for pslbm_sync).  Any
  * output pointer may be NULL. */
