@@ -311,7 +311,10 @@ pslbm_status pslbm_batch_destroy(pslbm_batch_t b);
  * each pslbm_server_advance() admits queued requests in arrival order while
  * the device-memory estimate of the resident simulations stays within
  * hbm_budget_bytes (and their count within max_active), re-packs the resident
- * simulations into batches when the set changed, advances them by chunk_steps
+ * simulations into batches when the set changed (one per species count; the
+ * first batch of a species count chooses the kernel variant by timing when a
+ * chunk is long enough, and the batches re-packed after it take that variant),
+ * advances them by chunk_steps
  * steps (a simulation is frozen at its step budget), and retires requests that
  * reached their step budget or whose total solid volume changed by at least
  * their stop fraction (checked after each chunk).  Retired requests keep their
